@@ -1,0 +1,71 @@
+"""The pins catch plausible mistakes: each test plants one mistake in a copy of
+the oracle (on the CPU) and checks that the matching closed form no longer holds."""
+import math
+
+import numpy as np
+import pytest
+
+import sn_inputs as si
+from oracle import CartesianOracle, product_quadrature, run
+from oracle import cartesian as cart
+from test_oracle_cartesian import uniform_problem, quad_custom
+
+
+def _decay_error(op, dt=0.05, n=20, sa=0.9, Q=0.25):
+    psi, _, _ = run(op, np.full((op.nx * op.ny, op.M), 0.8), dt, n, "euler")
+    ph = 0.8 * 2 * math.pi
+    for _ in range(n):
+        ph = ph + dt * (-sa * ph + 2 * math.pi * Q)
+    return np.max(np.abs(op.phi(psi) / ph - 1))
+
+
+def test_dropped_scattering_term_is_caught():
+    q = product_quadrature(2, 8)
+    p = uniform_problem(4, 4, 1.0, 0.9, 0.6, Q=0.25, kind=(2, 2, 2, 2))
+    good = CartesianOracle(p, q, order=1)
+    assert _decay_error(good) < 1e-13
+
+    class NoScatter(CartesianOracle):
+        def F(self, psi):
+            return -self.flux_sum(psi) / self.area - self.sigma_t[:, None] * psi + self.Q[:, None]
+    assert _decay_error(NoScatter(p, q, order=1)) > 1e-3
+
+
+def test_downwind_trace_is_caught():
+    nx, sigma = 20, 1.5
+    q = quad_custom([0.8], [0.0])
+    p = uniform_problem(nx, 1, 1.0, sigma, 0.0, kind=(si.INFLOW, 0, 0, 0), inflow=(1.0, 0, 0, 0), Ly=0.1)
+    dx = 1.0 / nx
+    prof = ((0.8 / (0.8 + sigma * dx)) ** (np.arange(nx) + 1))[:, None]
+
+    class Downwind(CartesianOracle):
+        def _face_traces(self, P, vel, g_lo, g_hi, periodic):
+            return super()._face_traces(P, -vel, g_lo, g_hi, periodic)
+    assert np.max(np.abs(CartesianOracle(p, q).F(prof))) < 1e-13
+    assert np.max(np.abs(Downwind(p, q).F(prof))) > 1e-2
+
+
+def test_unlimited_slope_is_caught(monkeypatch):
+    n = 16
+    q = product_quadrature(2, 8)
+    p = uniform_problem(n, n, 1.0, 0.0, 0.0, kind=(2, 2, 2, 2))
+    xc, yc = p.mesh.centres()
+    psi0 = np.where((np.abs(xc - 0.5) < 0.2) & (np.abs(yc - 0.5) < 0.25), 2.0, 0.5)[:, None] * np.ones(16)[None, :]
+    dt = 0.6 / (np.max(np.abs(q[0]) + np.abs(q[1])) * n)
+    monkeypatch.setattr(cart, "minmod", lambda a, b: 0.5 * (a + b))
+    psi, _, _ = run(CartesianOracle(p, q, order=2), psi0, dt, 40, "heun")
+    assert psi.max() > 2.0 + 1e-3 or psi.min() < 0.5 - 1e-3
+
+
+def test_wrong_heun_average_is_caught():
+    q = product_quadrature(2, 8)
+    p = uniform_problem(4, 4, 1.0, 0.9, 0.6, Q=0.0, kind=(2, 2, 2, 2))
+    op = CartesianOracle(p, q, order=1)
+    psi = np.full((16, 16), 1.0)
+    dt, sa = 0.1, 0.9
+    # Heun as printed: (psi + psi2)/2; a variant that returns psi2 is first order and fails the recurrence
+    psi1 = psi + dt * op.F(psi)
+    psi2 = psi1 + dt * op.F(psi1)
+    g_heun = 1 - sa * dt + 0.5 * (sa * dt) ** 2
+    assert np.allclose(op.phi(0.5 * (psi + psi2)), 2 * math.pi * g_heun, rtol=1e-14)
+    assert not np.allclose(op.phi(psi2), 2 * math.pi * g_heun, rtol=1e-6)
