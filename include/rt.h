@@ -1,0 +1,283 @@
+/*
+ * rt.h - C ABI of the GB300 (sm_103a) explicit S_N transport step.
+ *
+ * One solver advances the 2-D discrete-ordinates system with isotropic
+ * scattering (Sec. 4.1, Eq. sn_2d)
+ *
+ *   d/dt psi_k + xi_k d/dx psi_k + eta_k d/dy psi_k + sigma_t psi_k
+ *       = sigma_s/(2 pi) sum_l w_l psi_l + Q,      sum_k w_k = 2 pi,
+ *
+ * discretised by cell-centred finite volumes with upwind traces (Sec. 4.2,
+ * Eq. sn_2d_eqn_fv and Eq. upwind1stOrder; first order, or MUSCL with a
+ * minmod limiter on Cartesian grids), ghost cells holding psi^- on boundary
+ * faces with first-order boundary fluxes (Sec. 4.2), and forward Euler or
+ * Heun's method with uniform dt = T/N_t (Sec. 4.3). Every step runs in CUDA
+ * kernels on the caller's stream; the host only validates, derives mesh
+ * metadata once and enqueues launches.
+ *
+ * Conventions
+ *   - All array arguments are host pointers unless stated. Inputs are copied
+ *     during rt_create; the caller keeps ownership of its arrays.
+ *   - Device memory comes only from rt_options.alloc/free (cudaMalloc and
+ *     cudaFree when alloc is NULL). Launches and copies go to rt_options.stream
+ *     (a cudaStream_t; NULL = legacy default stream) on the device that is
+ *     current when rt_create is called.
+ *   - psi is stored ordinate-innermost: psi[cell][k], k = 0..M-1, padded on the
+ *     device to a multiple of 32 ordinates with zero-weight ordinates.
+ *     Cartesian cell id = j*nx + i (x fastest).
+ *   - Functions return rt_status; no exception crosses the ABI. The message of
+ *     the last failure on the calling thread is rt_last_error().
+ *   - After a device error, a wait that ran out (RT_ETIMEOUT) or a non-finite
+ *     QoI (RT_ENONFINITE) the solver enters an error state: every later call
+ *     but rt_destroy returns RT_ESTATE.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_EINVAL = 1,      /* an argument is invalid; nothing was changed */
+  RT_ENOMEM = 2,      /* the allocator returned NULL */
+  RT_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+  RT_ETIMEOUT = 4,    /* a bounded device-side wait ran out */
+  RT_ENONFINITE = 5,  /* the solution became non-finite (NaN/Inf in a QoI) */
+  RT_ESTATE = 6       /* the solver is in its error state */
+} rt_status;
+
+enum { RT_MESH_CARTESIAN = 0, RT_MESH_TRIANGLES = 1 };
+enum { RT_BC_VACUUM = 0, RT_BC_INFLOW = 1, RT_BC_PERIODIC = 2 };
+enum { RT_EULER = 0, RT_HEUN = 1 };
+enum { RT_FP32 = 0, RT_BF16 = 1 };
+enum { RT_SIDE_XMIN = 0, RT_SIDE_XMAX = 1, RT_SIDE_YMIN = 2, RT_SIDE_YMAX = 3 };
+
+#define RT_MAX_MATERIALS 16
+#define RT_MAX_REGIONS 16
+
+/* Spatial mesh (Sec. 4.2).
+ *   kind = RT_MESH_CARTESIAN: nx x ny rectangles of size dx x dy with lower-left
+ *     corner (x0, y0); cell id j*nx + i.
+ *   kind = RT_MESH_TRIANGLES: n_vert vertices vxy[2*v + {0,1}] and n_tri
+ *     counter-clockwise triangles tri[3*t + {0,1,2}] (vertex ids). Edges used by
+ *     one triangle only are boundary edges; each is assigned to the side
+ *     (x-, x+, y-, y+) of the vertices' bounding box nearest to its midpoint.
+ *     Local edge e of a triangle runs from its vertex e to vertex (e+1)%3. */
+typedef struct {
+  int32_t kind;
+  int32_t nx, ny;
+  double x0, y0, dx, dy;
+  int64_t n_vert;
+  const double* vxy;
+  int64_t n_tri;
+  const int32_t* tri;
+} rt_mesh;
+
+/* Piecewise-constant materials (Sec. 3.1, 3.2): per material sigma_a, sigma_s
+ * (sigma_t = sigma_a + sigma_s) and isotropic source Q; per cell a material id
+ * (0..n_mat-1) and a QoI region id (0..n_regions-1). n_mat, n_regions <= 16. */
+typedef struct {
+  int32_t n_mat;
+  const double* sigma_a;
+  const double* sigma_s;
+  const double* Q;
+  const int32_t* cell_mat;
+  const int32_t* cell_region;
+  int32_t n_regions;
+} rt_materials;
+
+/* Ordinates on the upper hemisphere (Sec. 4.1): direction components xi_k,
+ * eta_k (|(xi,eta)| <= 1) and weights w_k, k = 0..M-1. The weights should sum
+ * to 2 pi (the scattering term uses sigma_s/(2 pi) sum_l w_l psi_l). */
+typedef struct {
+  int64_t M;
+  const double* xi;
+  const double* eta;
+  const double* w;
+} rt_quadrature;
+
+/* Boundary per side (x-, x+, y-, y+): RT_BC_VACUUM (psi^- = 0), RT_BC_INFLOW
+ * (isotropic psi^- = inflow[side] for ordinates entering through that side) or
+ * RT_BC_PERIODIC (accepted by rt_create only on the CPU oracle side; the GPU
+ * path rejects it with RT_EINVAL). */
+typedef struct {
+  int32_t side_kind[4];
+  double inflow[4];
+} rt_boundary;
+
+typedef void* (*rt_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*rt_free_fn)(void* ptr, void* ctx);
+
+/* Solver options.
+ *   order: 1 (first-order upwind) or 2 (MUSCL-minmod; Cartesian only).
+ *   integrator: RT_EULER or RT_HEUN.  storage: RT_FP32 or RT_BF16 (psi storage;
+ *     arithmetic is FP32 either way, QoI accumulation FP64).
+ *   dt > 0: target step; N_t = ceil(t_end/dt - 1e-9) and dt = t_end/N_t.
+ *   dt <= 0: Cartesian 0.5*min(dx,dy); triangles 0.9*min_i 2 A_i / P_i.
+ *   tile_x, tile_y: Cartesian tile (cells per strip in x: 32 or 64; rows per
+ *     segment); 0 = chosen by the library.
+ *   alloc/free/alloc_ctx: device allocator (NULL = cudaMalloc/cudaFree).
+ *   stream: cudaStream_t for every launch and copy. */
+typedef struct {
+  int32_t order;
+  int32_t integrator;
+  int32_t storage;
+  int32_t tile_x;
+  int32_t tile_y;
+  int32_t reserved;
+  double dt;
+  double t_end;
+  rt_alloc_fn alloc;
+  rt_free_fn free;
+  void* alloc_ctx;
+  void* stream;
+} rt_options;
+
+/* QoIs (Sec. 3.1 QoI-3..5, Sec. 3.2 QoI-2, QoI-7), FP64:
+ *   abs_now[r]  = sum_{i in region r} A_i sigma_a,i phi_i at time t
+ *   abs_int[r]  = time integral of abs_now[r] over [0, t]
+ *   mass        = sum_i A_i phi_i at time t
+ *   outflow_now = sum over boundary faces of l sum_k w_k (omega_k . n) psi_hat_k
+ *   outflow_int = its time integral; source_int = t * 2 pi sum_i A_i Q_i.
+ * Time integrals use the weights of the scheme (Euler: dt*S(psi^n); Heun:
+ * dt/2*(S(psi^n) + S(psi^(1)))), so mass + sum(abs_int) + outflow_int equals
+ * mass(0) + source_int up to rounding. */
+typedef struct {
+  double t;
+  int64_t step;
+  int64_t n_steps;
+  int32_t n_regions;
+  int32_t status;
+  double abs_now[RT_MAX_REGIONS];
+  double abs_int[RT_MAX_REGIONS];
+  double mass;
+  double outflow_now;
+  double outflow_int;
+  double source_int;
+} rt_qoi_t;
+
+/* Static facts about a solver. */
+typedef struct {
+  int64_t n_cells;
+  int64_t M;
+  int64_t M_pad;
+  int64_t n_steps;
+  double dt;
+  double t_end;
+  int32_t kind, order, integrator, storage;
+  int32_t tile_x, tile_y, n_work_items, stages_per_step;
+  int64_t device_bytes;
+} rt_info_t;
+
+typedef struct rt_solver rt_solver;
+
+/* Product quadrature (Sec. 4.1 with the tensorised Gauss-Legendre rule named in
+ * Sec. 5.1.1): n_p Gauss-Legendre points on mu in [0,1] times n_phi azimuths
+ * varphi_a = (a + 1/2) 2 pi / n_phi; k = a*n_p + p; xi = sqrt(1-mu^2) cos varphi,
+ * eta = sqrt(1-mu^2) sin varphi (Eq. polar_coordinates), w = w_p * 2 pi/n_phi
+ * (sum 2 pi). Writes n_p*n_phi values to each host array (mu may be NULL).
+ * RT_EINVAL if n_p < 1, n_p > 64, n_phi < 1 or an output pointer is NULL. */
+rt_status rt_quad_product(int32_t n_p, int32_t n_phi, double* xi, double* eta, double* mu, double* w);
+
+/* Create a solver for one problem: validates, derives per-cell metadata
+ * (triangles: areas, n*l/A per edge, neighbours, boundary sides), allocates
+ * device state, sets psi(0) = 0 and evaluates phi and the QoI integrands of the
+ * initial state. RT_EINVAL on invalid input (message in rt_last_error),
+ * RT_ENOMEM if the allocator fails, RT_ECUDA on a CUDA failure. On failure
+ * *out is NULL and nothing is leaked. */
+rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
+                    const rt_boundary* bc, const rt_options* opts, rt_solver** out);
+
+/* Enqueue n time steps (clamped at N_t) on the solver's stream; returns after
+ * enqueueing. Each step is one launch (Euler) or two (Heun stages). */
+rt_status rt_step(rt_solver* s, int64_t n);
+
+/* Synchronise the stream and copy the QoIs to *out (about 300 bytes). Returns
+ * RT_ETIMEOUT / RT_ENONFINITE (and enters the error state) if a kernel
+ * reported one. */
+rt_status rt_qoi(rt_solver* s, rt_qoi_t* out);
+
+/* Static facts (no synchronisation). */
+rt_status rt_info(const rt_solver* s, rt_info_t* out);
+
+/* Copy psi (n = n_cells*M doubles, [cell][k]) or phi (n = n_cells doubles) of the
+ * current state to host memory; synchronises. RT_EINVAL if n is wrong. */
+rt_status rt_get_psi(rt_solver* s, double* host, int64_t n);
+rt_status rt_get_phi(rt_solver* s, double* host, int64_t n);
+
+/* Replace the current state by psi (n = n_cells*M doubles, [cell][k]); rounds to
+ * the storage type, recomputes phi and the QoI integrands. Time, step count and
+ * time integrals are kept. Synchronises. */
+rt_status rt_set_psi(rt_solver* s, const double* host, int64_t n);
+
+/* Device view of the current state: psi (storage type, [cell][M_pad]) and phi
+ * (float, [cell]). Pointers stay owned by the solver and are valid until the
+ * next rt_step (Euler alternates two buffers) or rt_destroy. */
+rt_status rt_device_state(rt_solver* s, void** psi, void** phi, int32_t* storage);
+
+/* Checkpoint: the full state (psi as stored, phi, step, time integrals, current
+ * integrands) as an opaque byte blob of rt_state_size() bytes. rt_set_state
+ * restores a blob taken from a solver created with the same arguments; a run
+ * resumed from it matches the uninterrupted run bit for bit. Both synchronise. */
+rt_status rt_state_size(const rt_solver* s, size_t* bytes);
+rt_status rt_get_state(rt_solver* s, void* host, size_t bytes);
+rt_status rt_set_state(rt_solver* s, const void* host, size_t bytes);
+
+/* Test hooks, not for production use: key "wait_limit_cycles" bounds every
+ * device-side wait (default about two seconds of SM clock); key "drop_load"
+ * (value q >= 0) makes the Cartesian kernel skip its q-th tile load, so that the
+ * wait for it runs out and the launch reports RT_ETIMEOUT. value < 0 clears. */
+rt_status rt_debug_set(rt_solver* s, const char* key, int64_t value);
+
+void rt_destroy(rt_solver* s);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* rt_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent problems advanced together by shared launches.
+ * Each stage is one launch over the work items of every unfinished problem
+ * (finished problems are masked on the device), and rt_batch_run replays a
+ * CUDA graph of `graph_steps` steps until every problem reaches its own N_t.
+ * The paper has no batching; problems are the lattice design-parameter
+ * sweeps of Sec. 3.1.3 (DP-1) solved side by side.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  rt_mesh mesh;
+  rt_materials mat;
+  rt_quadrature quad;
+  rt_boundary bc;
+  int32_t order;
+  int32_t integrator;
+  double dt;
+  double t_end;
+} rt_problem;
+
+typedef struct rt_batch rt_batch;
+
+/* Create a batch of k problems sharing storage type, allocator and stream from
+ * opts (opts.order/integrator/dt/t_end are ignored; each problem has its own).
+ * All problems must use the same integrator. Errors as rt_create. */
+rt_status rt_batch_create(int32_t k, const rt_problem* problems, const rt_options* opts, rt_batch** out);
+
+/* Advance every problem to its own N_t (at most max_steps steps per problem when
+ * max_steps > 0); enqueues graph replays on the stream and returns. */
+rt_status rt_batch_run(rt_batch* b, int64_t max_steps);
+
+/* Synchronise and copy problem i's QoIs. */
+rt_status rt_batch_qoi(rt_batch* b, int32_t i, rt_qoi_t* out);
+
+/* Copy problem i's psi ([cell][k] doubles, n = n_cells*M). */
+rt_status rt_batch_get_psi(rt_batch* b, int32_t i, double* host, int64_t n);
+
+void rt_batch_destroy(rt_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_GB300_H */

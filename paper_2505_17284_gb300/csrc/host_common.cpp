@@ -1,0 +1,570 @@
+// Instance construction for the S_N step: validation, mesh metadata (Sec. 4.2),
+// time step (Sec. 4.3), device buffers, TMA tensor maps and work items.
+#include "host_common.h"
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <unordered_map>
+
+namespace rtk {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+void clear_error() { g_last_error.clear(); }
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+rt_status DeviceArena::get(size_t n, void** out) {
+  *out = nullptr;
+  if (n == 0) n = 256;
+  n = (n + 255) / 256 * 256;
+  void* p = nullptr;
+  if (alloc_fn) {
+    p = alloc_fn(n, ctx);
+    if (!p) {
+      set_error("allocator returned NULL for %zu bytes", n);
+      return RT_ENOMEM;
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      set_error("cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+    }
+  }
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0) {
+    set_error("allocator returned a pointer that is not 16-byte aligned");
+    if (free_fn) free_fn(p, ctx); else cudaFree(p);
+    return RT_EINVAL;
+  }
+  owned.push_back(p);
+  bytes += (int64_t)n;
+  *out = p;
+  return RT_OK;
+}
+
+void DeviceArena::release(void* p) {
+  auto it = std::find(owned.begin(), owned.end(), p);
+  if (it == owned.end()) return;
+  owned.erase(it);
+  if (free_fn) free_fn(p, ctx); else cudaFree(p);
+}
+
+void DeviceArena::free_all() {
+  for (void* p : owned) {
+    if (free_fn) free_fn(p, ctx); else cudaFree(p);
+  }
+  owned.clear();
+}
+
+int device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return n;
+}
+
+// ---------------------------------------------------------------- tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static rt_status encode_psi_map(CUtensorMap* map, void* base, int storage, int Mpad, int nx, int ny, int box_x) {
+  auto enc = get_encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return RT_ECUDA;
+  }
+  const size_t es = storage == RT_BF16 ? 2 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)Mpad, (cuuint64_t)nx, (cuuint64_t)ny};
+  cuuint64_t strides[2] = {(cuuint64_t)Mpad * es, (cuuint64_t)nx * Mpad * es};
+  cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)box_x, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = enc(map, storage == RT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for dims {%d,%d,%d} box_x %d", (int)r, Mpad, nx, ny, box_x);
+    return RT_ECUDA;
+  }
+  return RT_OK;
+}
+
+// ---------------------------------------------------------------- validation
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+static rt_status validate_common(const rt_materials* mat, const rt_quadrature* quad, const rt_boundary* bc,
+                                 int order, int integrator, int storage, double t_end, int64_t n_cells) {
+  if (!mat || !quad || !bc) { set_error("materials, quadrature and boundary are required"); return RT_EINVAL; }
+  if (order != 1 && order != 2) { set_error("order must be 1 or 2 (got %d)", order); return RT_EINVAL; }
+  if (integrator != RT_EULER && integrator != RT_HEUN) { set_error("integrator must be RT_EULER or RT_HEUN"); return RT_EINVAL; }
+  if (storage != RT_FP32 && storage != RT_BF16) { set_error("storage must be RT_FP32 or RT_BF16"); return RT_EINVAL; }
+  if (!(t_end > 0.0) || !std::isfinite(t_end)) { set_error("t_end must be positive and finite"); return RT_EINVAL; }
+  if (mat->n_mat < 1 || mat->n_mat > RT_MAX_MATERIALS) { set_error("n_mat must be in 1..%d", RT_MAX_MATERIALS); return RT_EINVAL; }
+  if (mat->n_regions < 1 || mat->n_regions > RT_MAX_REGIONS) { set_error("n_regions must be in 1..%d", RT_MAX_REGIONS); return RT_EINVAL; }
+  if (!mat->sigma_a || !mat->sigma_s || !mat->Q || !mat->cell_mat || !mat->cell_region) {
+    set_error("material arrays must not be NULL"); return RT_EINVAL;
+  }
+  for (int m = 0; m < mat->n_mat; ++m) {
+    if (!finite_nonneg(mat->sigma_a[m]) || !finite_nonneg(mat->sigma_s[m]) || !std::isfinite(mat->Q[m])) {
+      set_error("material %d: sigma_a, sigma_s must be finite and >= 0, Q finite", m); return RT_EINVAL;
+    }
+  }
+  for (int64_t i = 0; i < n_cells; ++i) {
+    if (mat->cell_mat[i] < 0 || mat->cell_mat[i] >= mat->n_mat) { set_error("cell %lld: material id %d out of range", (long long)i, mat->cell_mat[i]); return RT_EINVAL; }
+    if (mat->cell_region[i] < 0 || mat->cell_region[i] >= mat->n_regions) { set_error("cell %lld: region id %d out of range", (long long)i, mat->cell_region[i]); return RT_EINVAL; }
+  }
+  if (quad->M < 1 || quad->M > 65536 || !quad->xi || !quad->eta || !quad->w) { set_error("quadrature: need 1 <= M <= 65536 and non-NULL arrays"); return RT_EINVAL; }
+  for (int64_t k = 0; k < quad->M; ++k) {
+    const double x = quad->xi[k], y = quad->eta[k], w = quad->w[k];
+    if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(w) || x * x + y * y > 1.0 + 1e-12 || w < 0.0) {
+      set_error("ordinate %lld: need finite xi, eta with xi^2 + eta^2 <= 1 and w >= 0", (long long)k); return RT_EINVAL;
+    }
+  }
+  for (int s = 0; s < 4; ++s) {
+    const int k = bc->side_kind[s];
+    if (k == RT_BC_PERIODIC) { set_error("periodic sides are not supported by the GPU path"); return RT_EINVAL; }
+    if (k != RT_BC_VACUUM && k != RT_BC_INFLOW) { set_error("side %d: unknown boundary kind %d", s, k); return RT_EINVAL; }
+    if (k == RT_BC_INFLOW && !std::isfinite(bc->inflow[s])) { set_error("side %d: inflow must be finite", s); return RT_EINVAL; }
+  }
+  return RT_OK;
+}
+
+static int64_t steps_for(double t_end, double dt_target) {
+  const double r = t_end / dt_target - 1e-9;
+  int64_t n = (int64_t)std::ceil(r);
+  return n < 1 ? 1 : n;
+}
+
+// ---------------------------------------------------------------- triangles
+struct TriMeta {
+  std::vector<int4> nbr;
+  std::vector<float4> geo;
+  std::vector<double> area;
+  double min_2a_over_p = 0;
+};
+
+static rt_status triangle_metadata(const rt_mesh* m, const int32_t* cell_mat, const int32_t* cell_reg, TriMeta& out) {
+  const int64_t nv = m->n_vert, nt = m->n_tri;
+  const double* V = m->vxy;
+  const int32_t* T = m->tri;
+  if (nv < 3 || nt < 1 || !V || !T) { set_error("triangle mesh: need n_vert >= 3, n_tri >= 1 and arrays"); return RT_EINVAL; }
+  if (nt > (int64_t)0x7fffffff / 2) { set_error("triangle mesh too large"); return RT_EINVAL; }
+  double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+  for (int64_t v = 0; v < nv; ++v) {
+    const double x = V[2 * v], y = V[2 * v + 1];
+    if (!std::isfinite(x) || !std::isfinite(y)) { set_error("vertex %lld is not finite", (long long)v); return RT_EINVAL; }
+    xmin = std::min(xmin, x); xmax = std::max(xmax, x); ymin = std::min(ymin, y); ymax = std::max(ymax, y);
+  }
+  out.nbr.assign(nt, int4{0, 0, 0, 0});
+  out.geo.assign(2 * nt, float4{0, 0, 0, 0});
+  out.area.assign(nt, 0.0);
+  std::vector<int32_t> link(3 * nt, -1);
+  std::unordered_map<uint64_t, int64_t> edges;
+  edges.reserve((size_t)(nt * 2));
+  double min_ratio = INFINITY;
+  for (int64_t t = 0; t < nt; ++t) {
+    int32_t a[3] = {T[3 * t], T[3 * t + 1], T[3 * t + 2]};
+    for (int e = 0; e < 3; ++e)
+      if (a[e] < 0 || a[e] >= nv) { set_error("triangle %lld: vertex id out of range", (long long)t); return RT_EINVAL; }
+    if (a[0] == a[1] || a[1] == a[2] || a[0] == a[2]) { set_error("triangle %lld is degenerate", (long long)t); return RT_EINVAL; }
+    const double ax = V[2 * a[0]], ay = V[2 * a[0] + 1];
+    const double bx = V[2 * a[1]], by = V[2 * a[1] + 1];
+    const double cx = V[2 * a[2]], cy = V[2 * a[2] + 1];
+    const double A = 0.5 * ((bx - ax) * (cy - ay) - (by - ay) * (cx - ax));
+    if (!(A > 0.0)) { set_error("triangle %lld is not counter-clockwise (area %g)", (long long)t, A); return RT_EINVAL; }
+    out.area[t] = A;
+    double P = 0.0;
+    for (int e = 0; e < 3; ++e) {
+      const int32_t p = a[e], q = a[(e + 1) % 3];
+      P += std::hypot(V[2 * q] - V[2 * p], V[2 * q + 1] - V[2 * p + 1]);
+      const uint64_t key = ((uint64_t)(uint32_t)std::min(p, q) << 32) | (uint32_t)std::max(p, q);
+      auto it = edges.find(key);
+      if (it == edges.end()) {
+        edges.emplace(key, 3 * t + e);
+      } else {
+        const int64_t other = it->second;
+        if (other < 0) { set_error("edge shared by more than two triangles"); return RT_EINVAL; }
+        const int64_t ot = other / 3;
+        const int oe = (int)(other % 3);
+        if (T[3 * ot + oe] != q) { set_error("triangles %lld and %lld have inconsistent orientation", (long long)ot, (long long)t); return RT_EINVAL; }
+        link[3 * t + e] = (int32_t)ot;
+        link[other] = (int32_t)t;
+        it->second = -1;
+      }
+    }
+    min_ratio = std::min(min_ratio, 2.0 * A / P);
+  }
+  out.min_2a_over_p = min_ratio;
+  for (int64_t t = 0; t < nt; ++t) {
+    const int32_t a[3] = {T[3 * t], T[3 * t + 1], T[3 * t + 2]};
+    const double A = out.area[t];
+    int32_t nb[3];
+    float ax[3], ay[3];
+    for (int e = 0; e < 3; ++e) {
+      const int32_t p = a[e], q = a[(e + 1) % 3];
+      const double px = V[2 * p], py = V[2 * p + 1], qx = V[2 * q], qy = V[2 * q + 1];
+      // outward normal times length of edge p->q for a counter-clockwise triangle
+      const double nlx = qy - py, nly = -(qx - px);
+      ax[e] = (float)(nlx / A);
+      ay[e] = (float)(nly / A);
+      if (link[3 * t + e] >= 0) {
+        nb[e] = link[3 * t + e];
+      } else {
+        const double mx = 0.5 * (px + qx), my = 0.5 * (py + qy);
+        const double dist[4] = {std::fabs(mx - xmin), std::fabs(mx - xmax), std::fabs(my - ymin), std::fabs(my - ymax)};
+        int side = 0;
+        for (int s = 1; s < 4; ++s)
+          if (dist[s] < dist[side]) side = s;
+        nb[e] = -1 - side;
+      }
+    }
+    out.nbr[t] = int4{nb[0], nb[1], nb[2], (int)(cell_mat[t] & 255) | ((int)(cell_reg[t] & 255) << 8)};
+    out.geo[2 * t] = float4{ax[0], ay[0], ax[1], ay[1]};
+    out.geo[2 * t + 1] = float4{ax[2], ay[2], (float)A, 0.f};
+  }
+  return RT_OK;
+}
+
+// ---------------------------------------------------------------- tiles
+static void choose_cart_tiles(Instance& I, int tile_x, int tile_y) {
+  I.tx = (tile_x == 64) ? 64 : 32;
+  I.n_strips = (I.nx + I.tx - 1) / I.tx;
+  const int sms = device_sm_count();
+  int ly = tile_y;
+  if (ly <= 0) {
+    // smallest grid that still fills every SM a few CTAs deep, with segments long
+    // enough that the 2H halo rows per segment stay a few percent of the reads
+    const int target = 3 * sms;
+    const int segs = std::max(1, (target + I.n_strips - 1) / I.n_strips);
+    ly = (I.ny + segs - 1) / segs;
+    ly = std::max(8, std::min(ly, 128));
+  }
+  ly = std::max(1, std::min(ly, 256));
+  I.ly = ly;
+  I.n_segs = (I.ny + ly - 1) / ly;
+}
+
+static void cell_range_items(int64_t n_cells, std::vector<WorkItem>& items) {
+  const int sms = device_sm_count();
+  int64_t per = (n_cells + 4LL * sms - 1) / (4LL * sms);
+  per = std::max<int64_t>(64, std::min<int64_t>(per, 1024));
+  per = (per + 7) / 8 * 8;
+  const int64_t n = (n_cells + per - 1) / per;
+  items.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    WorkItem w{};
+    w.inst = 0;
+    w.a = (int32_t)(i * per);
+    w.b = (int32_t)std::min<int64_t>(per, n_cells - i * per);
+    w.item = (int32_t)i;
+    w.count = (int32_t)n;
+    items.push_back(w);
+  }
+}
+
+// ---------------------------------------------------------------- build
+rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
+                         const rt_boundary* bc, int order, int integrator, int storage, double dt_target,
+                         double t_end, int tile_x, int tile_y, DeviceArena& arena, cudaStream_t stream,
+                         Instance& I, std::vector<std::vector<char>>& keep) {
+  if (!mesh) { set_error("mesh is NULL"); return RT_EINVAL; }
+  int64_t n_cells = 0;
+  if (mesh->kind == RT_MESH_CARTESIAN) {
+    if (mesh->nx < 1 || mesh->ny < 1 || !(mesh->dx > 0) || !(mesh->dy > 0) || !std::isfinite(mesh->dx) || !std::isfinite(mesh->dy)) {
+      set_error("Cartesian mesh: need nx, ny >= 1 and dx, dy > 0"); return RT_EINVAL;
+    }
+    n_cells = (int64_t)mesh->nx * mesh->ny;
+    if (n_cells > 0x7fffffffLL) { set_error("Cartesian mesh too large"); return RT_EINVAL; }
+  } else if (mesh->kind == RT_MESH_TRIANGLES) {
+    n_cells = mesh->n_tri;
+    if (order != 1) { set_error("triangle meshes support order 1 only"); return RT_EINVAL; }
+  } else {
+    set_error("unknown mesh kind %d", mesh->kind); return RT_EINVAL;
+  }
+  rt_status s = validate_common(mat, quad, bc, order, integrator, storage, t_end, n_cells);
+  if (s != RT_OK) return s;
+  if (std::isnan(dt_target)) { set_error("dt is not a number"); return RT_EINVAL; }
+
+  I.kind = mesh->kind; I.order = order; I.integrator = integrator; I.storage = storage;
+  I.n_cells = n_cells;
+  I.M = (int32_t)quad->M;
+  I.Mpad = (I.M + 31) / 32 * 32;
+  I.vec = I.Mpad >= 128 ? 4 : (I.Mpad >= 64 ? 2 : 1);
+  I.t_end = t_end;
+  I.n_regions = mat->n_regions;
+  const size_t es = storage == RT_BF16 ? 2 : 4;
+  if (I.kind == RT_MESH_CARTESIAN) {
+    I.nx = mesh->nx; I.ny = mesh->ny;
+  }
+
+  // --- triangles: mesh metadata
+  TriMeta tm;
+  if (I.kind == RT_MESH_TRIANGLES) {
+    s = triangle_metadata(mesh, mat->cell_mat, mat->cell_region, tm);
+    if (s != RT_OK) return s;
+  }
+
+  // --- time step (Sec. 4.3: uniform dt = T / N_t)
+  double dtt = dt_target;
+  if (!(dtt > 0.0)) {
+    dtt = (I.kind == RT_MESH_CARTESIAN) ? 0.5 * std::min(mesh->dx, mesh->dy) : 0.9 * tm.min_2a_over_p;
+  }
+  I.n_steps = steps_for(t_end, dtt);
+  I.dt = t_end / (double)I.n_steps;
+
+  // --- source rate 2 pi sum A Q (reported as source_int = t * rate)
+  double wsum = 0.0;
+  for (int64_t k = 0; k < quad->M; ++k) wsum += quad->w[k];
+  double aq = 0.0;
+  if (I.kind == RT_MESH_CARTESIAN) {
+    for (int64_t i = 0; i < n_cells; ++i) aq += mat->Q[mat->cell_mat[i]];
+    aq *= mesh->dx * mesh->dy;
+  } else {
+    for (int64_t i = 0; i < n_cells; ++i) aq += tm.area[i] * mat->Q[mat->cell_mat[i]];
+  }
+  I.source_rate = aq * wsum;
+
+  // --- tiles and work items
+  if (I.kind == RT_MESH_CARTESIAN) {
+    choose_cart_tiles(I, tile_x, tile_y);
+    I.stage_items.clear();
+    const int n = I.n_strips * I.n_segs;
+    for (int g = 0; g < I.n_segs; ++g)
+      for (int st = 0; st < I.n_strips; ++st) {
+        WorkItem w{};
+        w.inst = 0; w.a = st; w.b = g; w.item = (int32_t)I.stage_items.size(); w.count = n;
+        I.stage_items.push_back(w);
+      }
+    const int stage_hi = integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER;
+    I.cart_smem = cart_smem_bytes(order, storage, I.tx, I.ly, stage_hi);
+    if (I.cart_smem > 227 * 1024) { set_error("tile %dx%d needs %zu bytes of shared memory", I.tx, I.ly, I.cart_smem); return RT_EINVAL; }
+  } else {
+    cell_range_items(n_cells, I.stage_items);
+  }
+  cell_range_items(n_cells, I.init_items);
+
+  // --- device buffers
+  const size_t psi_bytes = (size_t)n_cells * I.Mpad * es;
+  void* p = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    if ((s = arena.get(psi_bytes, &p)) != RT_OK) return s;
+    I.psi[b] = p;
+    if ((s = arena.get((size_t)n_cells * 4, &p)) != RT_OK) return s;
+    I.phi[b] = (float*)p;
+  }
+  if ((s = arena.get(sizeof(InstState), &p)) != RT_OK) return s;
+  I.st = (InstState*)p;
+  const size_t n_part = std::max(I.stage_items.size(), I.init_items.size());
+  if ((s = arena.get(n_part * NQ * sizeof(double), &p)) != RT_OK) return s;
+  I.partials = (double*)p;
+
+  // host images of per-cell and per-ordinate data (kept alive until the stream syncs)
+  keep.emplace_back(3 * (size_t)I.Mpad * sizeof(float));
+  float* hq = reinterpret_cast<float*>(keep.back().data());
+  for (int k = 0; k < I.Mpad; ++k) {
+    const bool in = k < I.M;
+    hq[k] = in ? (float)quad->xi[k] : 0.f;
+    hq[I.Mpad + k] = in ? (float)quad->eta[k] : 0.f;
+    hq[2 * I.Mpad + k] = in ? (float)quad->w[k] : 0.f;
+  }
+  float* d_quad = nullptr;
+  if ((s = arena.get(3 * (size_t)I.Mpad * sizeof(float), &p)) != RT_OK) return s;
+  d_quad = (float*)p;
+  RT_CUDA_TRY(cudaMemcpyAsync(d_quad, hq, 3 * (size_t)I.Mpad * sizeof(float), cudaMemcpyHostToDevice, stream));
+
+  uint8_t* d_mat = nullptr;
+  uint8_t* d_reg = nullptr;
+  int4* d_nbr = nullptr;
+  float4* d_geo = nullptr;
+  if (I.kind == RT_MESH_CARTESIAN) {
+    keep.emplace_back(2 * (size_t)n_cells);
+    uint8_t* hm = reinterpret_cast<uint8_t*>(keep.back().data());
+    for (int64_t i = 0; i < n_cells; ++i) {
+      hm[i] = (uint8_t)mat->cell_mat[i];
+      hm[n_cells + i] = (uint8_t)mat->cell_region[i];
+    }
+    if ((s = arena.get(2 * (size_t)n_cells, &p)) != RT_OK) return s;
+    d_mat = (uint8_t*)p;
+    d_reg = d_mat + n_cells;
+    RT_CUDA_TRY(cudaMemcpyAsync(d_mat, hm, 2 * (size_t)n_cells, cudaMemcpyHostToDevice, stream));
+  } else {
+    keep.emplace_back(n_cells * sizeof(int4));
+    std::memcpy(keep.back().data(), tm.nbr.data(), n_cells * sizeof(int4));
+    const void* hn = keep.back().data();
+    keep.emplace_back(2 * n_cells * sizeof(float4));
+    std::memcpy(keep.back().data(), tm.geo.data(), 2 * n_cells * sizeof(float4));
+    const void* hg = keep.back().data();
+    if ((s = arena.get(n_cells * sizeof(int4), &p)) != RT_OK) return s;
+    d_nbr = (int4*)p;
+    if ((s = arena.get(2 * n_cells * sizeof(float4), &p)) != RT_OK) return s;
+    d_geo = (float4*)p;
+    RT_CUDA_TRY(cudaMemcpyAsync(d_nbr, hn, n_cells * sizeof(int4), cudaMemcpyHostToDevice, stream));
+    RT_CUDA_TRY(cudaMemcpyAsync(d_geo, hg, 2 * n_cells * sizeof(float4), cudaMemcpyHostToDevice, stream));
+  }
+  for (int b = 0; b < 2; ++b) {
+    RT_CUDA_TRY(cudaMemsetAsync(I.psi[b], 0, psi_bytes, stream));
+    RT_CUDA_TRY(cudaMemsetAsync(I.phi[b], 0, (size_t)n_cells * 4, stream));
+  }
+  RT_CUDA_TRY(cudaMemsetAsync(I.st, 0, sizeof(InstState), stream));
+  RT_CUDA_TRY(cudaMemsetAsync(I.partials, 0, n_part * NQ * sizeof(double), stream));
+
+  // --- descriptor
+  InstDesc& D = I.desc;
+  std::memset(&D, 0, sizeof(D));
+  if (I.kind == RT_MESH_CARTESIAN) {
+    for (int b = 0; b < 2; ++b)
+      if ((s = encode_psi_map(&D.tm_psi_halo[b], I.psi[b], storage, I.Mpad, I.nx, I.ny, I.tx + 2 * order)) != RT_OK) return s;
+    if ((s = encode_psi_map(&D.tm_psi_center, I.psi[0], storage, I.Mpad, I.nx, I.ny, I.tx)) != RT_OK) return s;
+  }
+  for (int b = 0; b < 2; ++b) { D.psi[b] = I.psi[b]; D.phi[b] = I.phi[b]; }
+  D.mat = d_mat; D.region = d_reg;
+  D.xi = d_quad; D.eta = d_quad + I.Mpad; D.w = d_quad + 2 * I.Mpad;
+  D.tri_nbr = d_nbr; D.tri_geo = d_geo;
+  D.st = I.st; D.partials = I.partials;
+  D.kind = I.kind; D.order = order; D.integrator = integrator; D.storage = storage;
+  D.nx = I.nx; D.ny = I.ny; D.M = I.M; D.Mpad = I.Mpad;
+  D.n_chunks = I.Mpad / kChunk; D.tx = I.tx; D.ly = I.ly; D.n_strips = I.n_strips;
+  D.n_segs = I.n_segs; D.n_items = (int32_t)I.stage_items.size(); D.n_regions = I.n_regions;
+  D.n_cells = n_cells; D.n_steps = I.n_steps;
+  D.wait_limit = 4000000000LL;   // about two seconds of SM clock
+  D.drop_load = -1;
+  if (I.kind == RT_MESH_CARTESIAN) {
+    D.inv_dx = (float)(1.0 / mesh->dx); D.inv_dy = (float)(1.0 / mesh->dy);
+    D.dx_d = mesh->dx; D.dy_d = mesh->dy; D.area_d = mesh->dx * mesh->dy;
+  }
+  D.dt = (float)I.dt; D.dt_d = I.dt;
+  for (int sd = 0; sd < 4; ++sd) D.ghost[sd] = bc->side_kind[sd] == RT_BC_INFLOW ? (float)bc->inflow[sd] : 0.f;
+  for (int m = 0; m < kMaxMat; ++m) {
+    const bool in = m < mat->n_mat;
+    const double sa = in ? mat->sigma_a[m] : 0.0, ss = in ? mat->sigma_s[m] : 0.0, q = in ? mat->Q[m] : 0.0;
+    D.sig_t[m] = (float)(sa + ss);
+    D.sig_s2pi[m] = (float)(ss / (2.0 * M_PI));
+    D.q_src[m] = (float)q;
+    D.sig_a[m] = sa;
+  }
+  I.device_bytes = arena.bytes;
+  return RT_OK;
+}
+
+rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
+                      int storage, int order, int tx, int ly_max, int vec, cudaStream_t stream) {
+  const int stages[2] = {integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
+  const int n_st = integrator == RT_HEUN ? 2 : 1;
+  for (int i = 0; i < n_st; ++i) {
+    cudaError_t e;
+    if (kind == RT_MESH_CARTESIAN)
+      e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, tx, ly_max, stream);
+    else
+      e = launch_tri_stage(d_desc, d_items, n_items, stages[i], storage, vec, stream);
+    if (e != cudaSuccess) {
+      set_error("stage launch failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  }
+  return RT_OK;
+}
+
+rt_status read_inst_state(const Instance& I, cudaStream_t stream, InstState* h) {
+  RT_CUDA_TRY(cudaMemcpyAsync(h, I.st, sizeof(InstState), cudaMemcpyDeviceToHost, stream));
+  RT_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (h->status == DEV_TIMEOUT) {
+    set_error("a device-side wait ran out (block %lld, load %lld)", (long long)(h->timeout_where >> 32),
+              (long long)(h->timeout_where & 0xffffffff));
+    return RT_ETIMEOUT;
+  }
+  if (h->status == DEV_NONFINITE) {
+    set_error("the solution became non-finite by step %lld", (long long)h->step);
+    return RT_ENONFINITE;
+  }
+  return RT_OK;
+}
+
+void fill_qoi(const Instance& I, const InstState& h, rt_qoi_t* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->step = h.step;
+  out->n_steps = I.n_steps;
+  out->t = (double)h.step * I.dt;
+  out->n_regions = I.n_regions;
+  out->status = h.status;
+  for (int r = 0; r < I.n_regions; ++r) {
+    out->abs_now[r] = h.S_cur[r];
+    out->abs_int[r] = h.I[r];
+  }
+  out->mass = h.S_cur[kQMass];
+  out->outflow_now = h.S_cur[kQOut];
+  out->outflow_int = h.I[kQOut];
+  out->source_int = out->t * I.source_rate;
+}
+
+static int64_t convert_chunk(const Instance& I) {
+  return std::max<int64_t>(1, std::min<int64_t>(I.n_cells, (64LL << 20) / (8LL * I.M)));
+}
+
+rt_status copy_psi_out(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf, double* host) {
+  const size_t es = I.storage == RT_BF16 ? 2 : 4;
+  const int64_t chunk = convert_chunk(I);
+  void* tmp = nullptr;
+  rt_status st = arena.get((size_t)chunk * I.M * 8, &tmp);
+  if (st != RT_OK) return st;
+  for (int64_t c0 = 0; c0 < I.n_cells; c0 += chunk) {
+    const int64_t nc = std::min(chunk, I.n_cells - c0);
+    const char* src = (const char*)I.psi[buf] + (size_t)c0 * I.Mpad * es;
+    cudaError_t e = launch_convert_out(src, (double*)tmp, nc, I.M, I.Mpad, I.storage, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host + c0 * I.M, tmp, (size_t)nc * I.M * 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      arena.release(tmp);
+      set_error("reading psi failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  }
+  arena.release(tmp);
+  return RT_OK;
+}
+
+rt_status copy_psi_in(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf, const double* host) {
+  const size_t es = I.storage == RT_BF16 ? 2 : 4;
+  const int64_t chunk = convert_chunk(I);
+  void* tmp = nullptr;
+  rt_status st = arena.get((size_t)chunk * I.M * 8, &tmp);
+  if (st != RT_OK) return st;
+  for (int64_t c0 = 0; c0 < I.n_cells; c0 += chunk) {
+    const int64_t nc = std::min(chunk, I.n_cells - c0);
+    char* dst = (char*)I.psi[buf] + (size_t)c0 * I.Mpad * es;
+    cudaError_t e = cudaMemcpyAsync(tmp, host + c0 * I.M, (size_t)nc * I.M * 8, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = launch_convert_in((const double*)tmp, dst, nc, I.M, I.Mpad, I.storage, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      arena.release(tmp);
+      set_error("writing psi failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  }
+  arena.release(tmp);
+  return RT_OK;
+}
+
+}  // namespace rtk

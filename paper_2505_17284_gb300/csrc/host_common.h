@@ -1,0 +1,86 @@
+// Host-side building blocks shared by the single-solver and batch entry points:
+// error reporting, the caller-provided allocator, and construction of one
+// problem instance (validation, mesh metadata, device buffers, tensor maps,
+// work items).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_internal.h"
+
+namespace rtk {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define RT_CUDA_TRY(expr)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      ::rtk::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RT_ECUDA;                                                                      \
+    }                                                                                       \
+  } while (0)
+
+// Device memory from the caller's allocator (cudaMalloc/cudaFree when none).
+struct DeviceArena {
+  rt_alloc_fn alloc_fn = nullptr;
+  rt_free_fn free_fn = nullptr;
+  void* ctx = nullptr;
+  std::vector<void*> owned;
+  int64_t bytes = 0;
+
+  rt_status get(size_t n, void** out);
+  void release(void* p);   // free one block now
+  void free_all();
+};
+
+struct Instance {
+  int32_t kind = 0, order = 1, integrator = RT_EULER, storage = RT_FP32;
+  int32_t nx = 0, ny = 0;
+  int64_t n_cells = 0;
+  int32_t M = 0, Mpad = 0, vec = 1;
+  double dt = 0, t_end = 0;
+  int64_t n_steps = 0;
+  int32_t tx = 32, ly = 32, n_strips = 0, n_segs = 0;
+  int32_t n_regions = 0;
+  double source_rate = 0;   // 2 pi sum_i A_i Q_i
+  size_t cart_smem = 0;
+  std::vector<WorkItem> stage_items;   // inst field set by the owner
+  std::vector<WorkItem> init_items;
+  // device buffers
+  void* psi[2] = {nullptr, nullptr};
+  float* phi[2] = {nullptr, nullptr};
+  InstState* st = nullptr;
+  double* partials = nullptr;
+  InstDesc desc;   // host image; pointers are device addresses
+  int64_t device_bytes = 0;
+};
+
+// Validate the problem and build an instance: derive metadata, allocate and fill
+// device buffers (asynchronously on `stream`; the caller synchronises), zero
+// psi and phi, encode tensor maps. `d_state_slot` etc. are allocated inside.
+rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
+                         const rt_boundary* bc, int order, int integrator, int storage, double dt, double t_end,
+                         int tile_x, int tile_y, DeviceArena& arena, cudaStream_t stream, Instance& inst,
+                         std::vector<std::vector<char>>& host_keepalive);
+
+int device_sm_count();
+
+// Launch the stage(s) of one time step for the given instances' work items.
+rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
+                      int storage, int order, int tx, int ly_max, int vec, cudaStream_t stream);
+
+// Synchronise `stream` and read an instance's device state; maps device status
+// codes to RT_ETIMEOUT / RT_ENONFINITE.
+rt_status read_inst_state(const Instance& I, cudaStream_t stream, InstState* h);
+void fill_qoi(const Instance& I, const InstState& h, rt_qoi_t* out);
+// Copy psi of buffer `buf` to host doubles [cell][M] through a bounded device buffer.
+rt_status copy_psi_out(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf, double* host);
+rt_status copy_psi_in(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf, const double* host);
+
+}  // namespace rtk

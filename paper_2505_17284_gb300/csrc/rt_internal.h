@@ -1,0 +1,100 @@
+// Internal layout shared by the host code and the kernels of the S_N step.
+// Device memory of one problem instance (all owned by the solver/batch):
+//   psi[2]        psi storage (float or bf16), [n_cells][Mpad], ordinate-innermost
+//   phi[2]        scalar flux phi = sum_k w_k psi_k, float [n_cells]
+//   mat, region   uint8 per cell (material id, QoI region id)
+//   quad          float xi[Mpad], eta[Mpad], w[Mpad] (padding: xi = eta = w = 0)
+//   tri_nbr/geo   triangles only: neighbours and (n*l)/A per local edge
+//   desc          InstDesc (tensor maps, pointers, constants)
+//   state         InstState (step, buffer parity, status, FP64 QoI sums)
+//   partials      FP64 per-work-item QoI partial sums [n_items][NQ]
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rtk {
+
+constexpr int kMaxMat = 16;
+constexpr int kMaxReg = 16;
+constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
+constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
+constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
+constexpr int kChunk = 32;             // ordinates per chunk (one per lane)
+
+enum Stage : int32_t { STAGE_EULER = 0, STAGE_HEUN1 = 1, STAGE_HEUN2 = 2, STAGE_INIT = 3 };
+enum Kind : int32_t { KIND_CART = 0, KIND_TRI = 1 };
+
+// Status codes written by kernels (same values as rt_status).
+enum DevStatus : int32_t { DEV_OK = 0, DEV_TIMEOUT = 4, DEV_NONFINITE = 5 };
+
+struct InstState {
+  int64_t step;          // completed steps
+  int32_t parity;        // Euler: index of the buffer holding psi^n
+  int32_t status;        // DevStatus
+  uint32_t ticket;       // work items finished in the current launch
+  int32_t pad0;
+  int64_t timeout_where; // diagnostic: encoded position of a wait that ran out
+  double S_cur[NQ];      // integrands at psi^n
+  double S_mid[NQ];      // Heun: integrands at psi^(1)
+  double I[NQ];          // time integrals (abs, -, outflow)
+};
+
+struct alignas(128) InstDesc {
+  // Cartesian tile loads (TMA). 3-D maps over psi: {Mpad, nx, ny}.
+  CUtensorMap tm_psi_halo[2];   // box {32, tx + 2h, 1}, per psi buffer
+  CUtensorMap tm_psi_center;    // box {32, tx, 1} over psi buffer 0 (Heun stage 2)
+
+  void* psi[2];
+  float* phi[2];
+  const uint8_t* mat;
+  const uint8_t* region;
+  const float* xi;
+  const float* eta;
+  const float* w;
+  const int4* tri_nbr;          // {nbr0, nbr1, nbr2, mat | region << 8}; nbr < 0: -1 - side
+  const float4* tri_geo;        // 2 per cell: {ax0, ay0, ax1, ay1}, {ax2, ay2, area, 0}; a = (n*l)/A
+  InstState* st;
+  double* partials;             // [n_items][NQ]
+
+  int32_t kind, order, integrator, storage;
+  int32_t nx, ny, M, Mpad;
+  int32_t n_chunks, tx, ly, n_strips;
+  int32_t n_segs, n_items, n_regions, pad1;
+  int64_t n_cells;
+  int64_t n_steps;
+  int64_t wait_limit;           // device wait bound in clock64 cycles
+  int64_t drop_load;            // test hook: skip this load (-1 = none)
+  float inv_dx, inv_dy, dt, pad2;
+  double dt_d, area_d, dx_d, dy_d;  // Cartesian cell area and sizes (FP64 QoIs)
+  float ghost[4];               // inflow value per side (entering ordinates)
+  float sig_t[kMaxMat];
+  float sig_s2pi[kMaxMat];      // sigma_s / (2 pi)
+  float q_src[kMaxMat];
+  double sig_a[kMaxMat];
+};
+
+struct WorkItem {
+  int32_t inst;       // index into the InstDesc array
+  int32_t a;          // Cartesian stage: strip; cell-range kernels: first cell
+  int32_t b;          // Cartesian stage: segment; cell-range kernels: number of cells
+  int32_t item;       // index of this item within its instance (partials row)
+  int32_t count;      // items of this instance in this launch (last one finalizes)
+  int32_t pad;
+};
+
+// Launchers (defined in the .cu files). All enqueue on `stream`.
+cudaError_t launch_cart_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
+                              int order, int storage, int tx, int ly_max, cudaStream_t stream);
+size_t cart_smem_bytes(int order, int storage, int tx, int ly, int stage);
+cudaError_t prepare_cart_stage(int stage, int order, int storage, int tx, int ly_max);
+cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
+                             int storage, int vec, cudaStream_t stream);
+cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
+                        int storage, cudaStream_t stream);
+cudaError_t launch_convert_in(const double* src, void* dst, int64_t n_cells, int M, int Mpad, int storage,
+                              cudaStream_t stream);
+cudaError_t launch_convert_out(const void* src, double* dst, int64_t n_cells, int M, int Mpad, int storage,
+                               cudaStream_t stream);
+
+}  // namespace rtk

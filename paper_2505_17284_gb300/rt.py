@@ -1,0 +1,419 @@
+"""Thin Python binding of the C ABI declared in include/rt.h.
+
+The functions keep the C names (rt_create, rt_step, rt_qoi, ...) and only
+marshal arguments; every step of the S_N path runs in the CUDA kernels of
+librt_gb300.so. Loading fails loudly when the library has not been built.
+
+`Solver` and `Batch` are small conveniences over the same calls: they build
+the C structs from numpy arrays, allocate device memory through PyTorch's
+caching allocator (callbacks handed to the library) and enqueue on PyTorch's
+current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "librt_gb300.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ETIMEOUT, RT_ENONFINITE, RT_ESTATE = range(7)
+RT_MESH_CARTESIAN, RT_MESH_TRIANGLES = 0, 1
+RT_BC_VACUUM, RT_BC_INFLOW, RT_BC_PERIODIC = 0, 1, 2
+RT_EULER, RT_HEUN = 0, 1
+RT_FP32, RT_BF16 = 0, 1
+RT_MAX_REGIONS = 16
+STATUS_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ETIMEOUT",
+                5: "RT_ENONFINITE", 6: "RT_ESTATE"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class rt_mesh(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32),
+                ("x0", C.c_double), ("y0", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
+                ("n_vert", C.c_int64), ("vxy", _dp), ("n_tri", C.c_int64), ("tri", _ip)]
+
+
+class rt_materials(C.Structure):
+    _fields_ = [("n_mat", C.c_int32), ("sigma_a", _dp), ("sigma_s", _dp), ("Q", _dp),
+                ("cell_mat", _ip), ("cell_region", _ip), ("n_regions", C.c_int32)]
+
+
+class rt_quadrature(C.Structure):
+    _fields_ = [("M", C.c_int64), ("xi", _dp), ("eta", _dp), ("w", _dp)]
+
+
+class rt_boundary(C.Structure):
+    _fields_ = [("side_kind", C.c_int32 * 4), ("inflow", C.c_double * 4)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class rt_options(C.Structure):
+    _fields_ = [("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("reserved", C.c_int32),
+                ("dt", C.c_double), ("t_end", C.c_double),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class rt_qoi_t(C.Structure):
+    _fields_ = [("t", C.c_double), ("step", C.c_int64), ("n_steps", C.c_int64),
+                ("n_regions", C.c_int32), ("status", C.c_int32),
+                ("abs_now", C.c_double * RT_MAX_REGIONS), ("abs_int", C.c_double * RT_MAX_REGIONS),
+                ("mass", C.c_double), ("outflow_now", C.c_double), ("outflow_int", C.c_double),
+                ("source_int", C.c_double)]
+
+
+class rt_info_t(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("M", C.c_int64), ("M_pad", C.c_int64), ("n_steps", C.c_int64),
+                ("dt", C.c_double), ("t_end", C.c_double),
+                ("kind", C.c_int32), ("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("n_work_items", C.c_int32),
+                ("stages_per_step", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class rt_problem(C.Structure):
+    _fields_ = [("mesh", rt_mesh), ("mat", rt_materials), ("quad", rt_quadrature), ("bc", rt_boundary),
+                ("order", C.c_int32), ("integrator", C.c_int32), ("dt", C.c_double), ("t_end", C.c_double)]
+
+
+# exported functions: name -> (restype, argtypes)
+SIGNATURES = {
+    "rt_quad_product": (C.c_int, [C.c_int32, C.c_int32, _dp, _dp, _dp, _dp]),
+    "rt_create": (C.c_int, [C.POINTER(rt_mesh), C.POINTER(rt_materials), C.POINTER(rt_quadrature),
+                            C.POINTER(rt_boundary), C.POINTER(rt_options), C.POINTER(C.c_void_p)]),
+    "rt_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "rt_qoi": (C.c_int, [C.c_void_p, C.POINTER(rt_qoi_t)]),
+    "rt_info": (C.c_int, [C.c_void_p, C.POINTER(rt_info_t)]),
+    "rt_get_psi": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
+    "rt_get_phi": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
+    "rt_set_psi": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
+    "rt_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
+    "rt_state_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "rt_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "rt_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "rt_debug_set": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
+    "rt_destroy": (None, [C.c_void_p]),
+    "rt_last_error": (C.c_char_p, []),
+    "rt_batch_create": (C.c_int, [C.c_int32, C.POINTER(rt_problem), C.POINTER(rt_options), C.POINTER(C.c_void_p)]),
+    "rt_batch_run": (C.c_int, [C.c_void_p, C.c_int64]),
+    "rt_batch_qoi": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(rt_qoi_t)]),
+    "rt_batch_get_psi": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64]),
+    "rt_batch_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librt_gb300.so and declare its signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2505_17284_gb300.build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _fns():
+    return load_library()
+
+
+class RTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code):
+    if code != RT_OK:
+        raise RTError(code, _fns().rt_last_error().decode())
+    return code
+
+
+# -- thin wrappers with the C names ------------------------------------------------------
+def rt_quad_product(n_p: int, n_phi: int):
+    M = n_p * n_phi
+    xi, eta, mu, w = (np.zeros(M) for _ in range(4))
+    check(_fns().rt_quad_product(n_p, n_phi, _ptr(xi), _ptr(eta), _ptr(mu), _ptr(w)))
+    return xi, eta, mu, w
+
+
+def rt_create(mesh, mat, quad, bc, opts):
+    h = C.c_void_p()
+    check(_fns().rt_create(C.byref(mesh), C.byref(mat), C.byref(quad), C.byref(bc), C.byref(opts), C.byref(h)))
+    return h
+
+
+def rt_step(h, n: int):
+    return check(_fns().rt_step(h, int(n)))
+
+
+def rt_qoi(h) -> rt_qoi_t:
+    q = rt_qoi_t()
+    check(_fns().rt_qoi(h, C.byref(q)))
+    return q
+
+
+def rt_info(h) -> rt_info_t:
+    i = rt_info_t()
+    check(_fns().rt_info(h, C.byref(i)))
+    return i
+
+
+def rt_get_psi(h, n_cells: int, M: int) -> np.ndarray:
+    out = np.empty((n_cells, M))
+    check(_fns().rt_get_psi(h, _ptr(out), out.size))
+    return out
+
+
+def rt_get_phi(h, n_cells: int) -> np.ndarray:
+    out = np.empty(n_cells)
+    check(_fns().rt_get_phi(h, _ptr(out), out.size))
+    return out
+
+
+def rt_set_psi(h, psi: np.ndarray):
+    a = np.ascontiguousarray(psi, dtype=np.float64)
+    return check(_fns().rt_set_psi(h, _ptr(a), a.size))
+
+
+def rt_device_state(h):
+    p, f, s = C.c_void_p(), C.c_void_p(), C.c_int32()
+    check(_fns().rt_device_state(h, C.byref(p), C.byref(f), C.byref(s)))
+    return p.value, f.value, s.value
+
+
+def rt_get_state(h) -> bytes:
+    n = C.c_size_t()
+    check(_fns().rt_state_size(h, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    check(_fns().rt_get_state(h, buf, n.value))
+    return buf.raw
+
+
+def rt_set_state(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    return check(_fns().rt_set_state(h, buf, len(blob)))
+
+
+def rt_debug_set(h, key: str, value: int):
+    return check(_fns().rt_debug_set(h, key.encode(), int(value)))
+
+
+def rt_destroy(h):
+    if h:
+        _fns().rt_destroy(h)
+
+
+def rt_last_error() -> str:
+    return _fns().rt_last_error().decode()
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+# -- conveniences --------------------------------------------------------------------------
+class _Keep:
+    """Holds the numpy arrays referenced by C structs until the call returns."""
+
+    def __init__(self):
+        self.refs = []
+
+    def f64(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.refs.append(a)
+        return a.ctypes.data_as(_dp)
+
+    def i32(self, a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        self.refs.append(a)
+        return a.ctypes.data_as(_ip)
+
+
+def make_structs(problem, quad, keep: _Keep):
+    """C structs for a problem from sn_inputs (mesh, materials, boundary) and a
+    quadrature (xi, eta, mu, w)."""
+    m = problem.mesh
+    mesh = rt_mesh()
+    if hasattr(m, "nx"):
+        mesh.kind = RT_MESH_CARTESIAN
+        mesh.nx, mesh.ny, mesh.x0, mesh.y0, mesh.dx, mesh.dy = m.nx, m.ny, m.x0, m.y0, m.dx, m.dy
+    else:
+        mesh.kind = RT_MESH_TRIANGLES
+        mesh.n_vert = m.vertices.shape[0]
+        mesh.vxy = keep.f64(m.vertices.reshape(-1))
+        mesh.n_tri = m.triangles.shape[0]
+        mesh.tri = keep.i32(m.triangles.reshape(-1))
+    mt = problem.materials
+    mat = rt_materials()
+    mat.n_mat = len(mt.sigma_a)
+    mat.sigma_a, mat.sigma_s, mat.Q = keep.f64(mt.sigma_a), keep.f64(mt.sigma_s), keep.f64(mt.Q)
+    mat.cell_mat, mat.cell_region = keep.i32(mt.cell_mat), keep.i32(mt.cell_region)
+    mat.n_regions = max(mt.n_regions, int(np.max(mt.cell_region)) + 1)
+    xi, eta, _, w = quad
+    q = rt_quadrature()
+    q.M = len(xi)
+    q.xi, q.eta, q.w = keep.f64(xi), keep.f64(eta), keep.f64(w)
+    bc = rt_boundary()
+    for s in range(4):
+        bc.side_kind[s] = int(problem.boundary.kind[s])
+        bc.inflow[s] = float(problem.boundary.inflow[s])
+    return mesh, mat, q, bc
+
+
+class TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the library as
+    C callbacks, plus the current stream of the current device."""
+
+    def __init__(self, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = torch.cuda.current_stream(self.device)
+
+        def _alloc(n, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(n), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _free(p, ctx):
+            if p:
+                torch.cuda.caching_allocator_delete(int(p))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+    def fill(self, opts: rt_options):
+        opts.alloc = self.alloc
+        opts.free = self.free
+        opts.alloc_ctx = None
+        opts.stream = self.stream.cuda_stream
+
+
+def make_options(order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=1.0, tile_x=0, tile_y=0,
+                 allocator: TorchAllocator | None = None, stream=None) -> rt_options:
+    o = rt_options()
+    o.order, o.integrator, o.storage = order, integrator, storage
+    o.tile_x, o.tile_y = tile_x, tile_y
+    o.dt, o.t_end = dt, t_end
+    if allocator is not None:
+        allocator.fill(o)
+    if stream is not None:
+        o.stream = stream
+    return o
+
+
+class Solver:
+    """One problem on the GPU: create -> step -> qoi, through the C ABI."""
+
+    def __init__(self, problem, quad, order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=None,
+                 tile_x=0, tile_y=0, use_torch_allocator=True):
+        keep = _Keep()
+        mesh, mat, q, bc = make_structs(problem, quad, keep)
+        self.allocator = TorchAllocator() if use_torch_allocator else None
+        opts = make_options(order, integrator, storage, dt, problem.t_end if t_end is None else t_end,
+                            tile_x, tile_y, self.allocator)
+        self.h = rt_create(mesh, mat, q, bc, opts)
+        self.info = rt_info(self.h)
+        self.n_cells, self.M = int(self.info.n_cells), int(self.info.M)
+        self.n_regions = mat.n_regions
+
+    def step(self, n=None):
+        rt_step(self.h, self.info.n_steps if n is None else n)
+        return self
+
+    def qoi(self) -> dict:
+        q = rt_qoi(self.h)
+        R = self.n_regions
+        return {"t": q.t, "step": q.step, "n_steps": q.n_steps, "abs_now": np.array(q.abs_now[:R]),
+                "abs_int": np.array(q.abs_int[:R]), "mass": q.mass, "outflow_now": q.outflow_now,
+                "outflow_int": q.outflow_int, "source_int": q.source_int}
+
+    def psi(self) -> np.ndarray:
+        return rt_get_psi(self.h, self.n_cells, self.M)
+
+    def phi(self) -> np.ndarray:
+        return rt_get_phi(self.h, self.n_cells)
+
+    def set_psi(self, psi):
+        rt_set_psi(self.h, psi)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many problems advanced together (rt_batch_*)."""
+
+    def __init__(self, problems, quads, order=2, integrator=RT_HEUN, storage=RT_FP32, dts=None,
+                 tile_x=0, tile_y=0, use_torch_allocator=True):
+        keep = _Keep()
+        k = len(problems)
+        arr = (rt_problem * k)()
+        self.shapes = []
+        for i, (p, qd) in enumerate(zip(problems, quads)):
+            mesh, mat, q, bc = make_structs(p, qd, keep)
+            arr[i].mesh, arr[i].mat, arr[i].quad, arr[i].bc = mesh, mat, q, bc
+            arr[i].order = order if not isinstance(order, (list, tuple)) else order[i]
+            arr[i].integrator = integrator
+            arr[i].dt = 0.0 if dts is None else float(dts[i])
+            arr[i].t_end = p.t_end
+            self.shapes.append((p.mesh.n_cells, len(qd[0]), mat.n_regions))
+        self.allocator = TorchAllocator() if use_torch_allocator else None
+        opts = make_options(storage=storage, tile_x=tile_x, tile_y=tile_y, allocator=self.allocator)
+        self.h = C.c_void_p()
+        check(_fns().rt_batch_create(k, arr, C.byref(opts), C.byref(self.h)))
+        self.k = k
+
+    def run(self, max_steps=0):
+        check(_fns().rt_batch_run(self.h, int(max_steps)))
+        return self
+
+    def qoi(self, i) -> dict:
+        q = rt_qoi_t()
+        check(_fns().rt_batch_qoi(self.h, i, C.byref(q)))
+        R = self.shapes[i][2]
+        return {"t": q.t, "step": q.step, "n_steps": q.n_steps, "abs_now": np.array(q.abs_now[:R]),
+                "abs_int": np.array(q.abs_int[:R]), "mass": q.mass, "outflow_now": q.outflow_now,
+                "outflow_int": q.outflow_int, "source_int": q.source_int}
+
+    def psi(self, i) -> np.ndarray:
+        n, M, _ = self.shapes[i]
+        out = np.empty((n, M))
+        check(_fns().rt_batch_get_psi(self.h, i, _ptr(out), out.size))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _fns().rt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (FP32 storage and arithmetic against FP64): relative L2 error of
+psi <= 1e-5 and relative error of every QoI <= 1e-4. Sizes are chosen so the
+oracle finishes in seconds while the grids still span several tiles, ragged
+tails in x and y, several ordinate chunks and both boundary kinds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import sn_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+PSI_TOL = 1e-5
+QOI_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2505_17284_gb300 import build, rt as rtmod
+    build.build()
+    rtmod.load_library()
+    return rtmod
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def rel(a, b, floor=1e-30):
+    return abs(a - b) / max(abs(b), floor)
+
+
+def oracle_op(problem, quad, order):
+    if isinstance(problem.mesh, si.CartesianMesh):
+        return oracle.CartesianOracle(problem, quad, order=order)
+    return oracle.TriangleOracle(problem, quad, order=order)
+
+
+def check_qoi(q, acc, S, n_regions, scale):
+    for r in range(n_regions):
+        assert abs(q["abs_int"][r] - acc.abs_int[r]) <= QOI_TOL * max(abs(acc.abs_int[r]), 1e-3 * scale), ("abs_int", r)
+        assert abs(q["abs_now"][r] - S["abs"][r]) <= QOI_TOL * max(abs(S["abs"][r]), 1e-3 * scale), ("abs_now", r)
+    assert rel(q["mass"], S["mass"]) <= QOI_TOL
+    assert abs(q["outflow_int"] - acc.outflow_int) <= QOI_TOL * max(abs(acc.outflow_int), 1e-3 * scale)
+    assert abs(q["outflow_now"] - S["outflow"]) <= QOI_TOL * max(abs(S["outflow"]), 1e-3 * scale)
+
+
+def run_pair(rt, problem, n_p, n_phi, order, integrator, steps, psi0=None, storage=0, dt=0.0, tile_y=0, tile_x=0):
+    quad_lib = rt.rt_quad_product(n_p, n_phi)
+    s = rt.Solver(problem, quad_lib, order=order, integrator=integrator, storage=storage, dt=dt,
+                  tile_x=tile_x, tile_y=tile_y)
+    M = n_p * n_phi
+    if psi0 is not None:
+        s.set_psi(psi0)
+    s.step(steps)
+    q = s.qoi()
+    psi = s.psi()
+    phi = s.phi()
+    info = s.info
+    s.close()
+    op = oracle_op(problem, oracle.product_quadrature(n_p, n_phi), order)
+    start = np.zeros((problem.mesh.n_cells, M)) if psi0 is None else psi0
+    ref, acc, S = oracle.run(op, start, info.dt, steps, "euler" if integrator == rt.RT_EULER else "heun")
+    return psi, phi, q, ref, acc, S, op, info
+
+
+# ------------------------------------------------------------------ lattice, first order
+def test_lattice_config1_full(rt):
+    """70^2 lattice, 4x16 ordinates, first-order upwind + Euler, dt = dx/2, 64 steps."""
+    p = si.lattice_problem(70)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, 1, rt.RT_EULER, 64, dt=0.05)
+    assert info.n_steps == 64 and q["step"] == 64 and abs(q["t"] - 3.2) < 1e-12
+    assert rel_l2(psi, ref) <= PSI_TOL
+    assert rel_l2(phi, op.phi(ref)) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+    # discrete mass balance holds on the device to FP32 rounding
+    bal = q["mass"] + sum(q["abs_int"]) + q["outflow_int"]
+    assert abs(bal / q["source_int"] - 1) < 1e-5
+
+
+@pytest.mark.parametrize("integrator", ["euler", "heun"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_lattice_ragged_tiles(rt, order, integrator):
+    """84^2 = 2*32 + 20 cells in x, segments of 24 rows (ragged in y),
+    4x32 = 128 ordinates (4 chunks): every tile/segment/chunk boundary."""
+    p = si.lattice_problem(84)
+    integ = rt.RT_EULER if integrator == "euler" else rt.RT_HEUN
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 32, order, integ, 12, dt=0.5 * p.mesh.dx,
+                                                  tile_y=24)
+    assert info.tile_y == 24
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+@pytest.mark.parametrize("order,integrator", [(1, "euler"), (2, "heun"), (2, "euler"), (1, "heun")])
+def test_random_state_one_step_elementwise(rt, order, integrator):
+    """A random non-negative state on a 100 x 100 lattice (ragged: 100 = 3*32 + 4),
+    one step: element-wise agreement with the oracle."""
+    p = si.lattice_problem(100)
+    M = 64
+    psi0 = si.random_psi(p.mesh.n_cells, M, seed=21)
+    integ = rt.RT_EULER if integrator == "euler" else rt.RT_HEUN
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, order, integ, 1, psi0=psi0, dt=0.5 * p.mesh.dx)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(psi - ref)) <= 2e-6 * scale
+    assert rel_l2(psi, ref) <= PSI_TOL
+    assert rel_l2(phi, op.phi(ref)) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_tile_width_64(rt):
+    p = si.lattice_problem(91)
+    psi0 = si.smooth_psi(p.mesh, 64, seed=3)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, 2, rt.RT_HEUN, 5, psi0=psi0, dt=0.5 * p.mesh.dx,
+                                                  tile_x=64)
+    assert info.tile_x == 64
+    assert rel_l2(psi, ref) <= PSI_TOL
+
+
+def test_cartesian_inflow_boundary(rt):
+    """Enclosure geometry on a 65^2 Cartesian grid: inflow psi^- = 1 on x = 0, MUSCL + Heun."""
+    p = si.enclosure_cartesian_problem(65)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 2, 16, 2, rt.RT_HEUN, 30, dt=0.5 * p.mesh.dx)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 4, scale=S["mass"])
+    assert q["outflow_int"] < 0
+
+
+def test_general_inflow_all_sides_and_odd_quadrature(rt):
+    """Inflow of different strengths on every side and an ordinate count that is
+    not a multiple of 32 (padding ordinates carry zero weight)."""
+    p = si.lattice_problem(40)
+    p.boundary = si.Boundary(kind=(1, 1, 1, 1), inflow=(1.0, 0.5, 0.25, 2.0))
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 3, 10, 2, rt.RT_HEUN, 15, dt=0.5 * p.mesh.dx)
+    assert info.M == 30 and info.M_pad == 32
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_muscl_heun_lattice_mass_balance_and_symmetry(rt):
+    p = si.lattice_problem(56)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, 2, rt.RT_HEUN, 40, dt=0.5 * p.mesh.dx)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    bal = q["mass"] + sum(q["abs_int"]) + q["outflow_int"]
+    assert abs(bal / q["source_int"] - 1) < 1e-5
+    ph = phi.reshape(56, 56)
+    assert np.max(np.abs(ph - ph[:, ::-1])) <= 1e-5 * ph.max()
+
+
+# ------------------------------------------------------------------ triangles
+@pytest.mark.parametrize("integrator", ["euler", "heun"])
+def test_enclosure_triangles(rt, integrator):
+    """Jittered split-square enclosure mesh (2*40^2 triangles), 4x16 ordinates."""
+    p = si.enclosure_problem(40, jitter=0.2, seed=0)
+    integ = rt.RT_EULER if integrator == "euler" else rt.RT_HEUN
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, 1, integ, 25)
+    n_ref, dt_ref = oracle.triangle_dt(op, p.t_end)
+    assert info.n_steps == n_ref and abs(info.dt - dt_ref) < 1e-15
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 4, scale=S["mass"] + sum(acc.abs_int))
+
+
+@pytest.mark.parametrize("n_p,n_phi", [(2, 16), (4, 16), (8, 32)])
+def test_triangle_random_state_vector_widths(rt, n_p, n_phi):
+    """Random state, one Euler step, ordinate counts 32/64/256 (1, 2 and 4
+    ordinates per lane per access)."""
+    p = si.enclosure_problem(18, jitter=0.2, seed=5)
+    M = n_p * n_phi
+    psi0 = si.random_psi(p.mesh.n_cells, M, seed=2)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, n_p, n_phi, 1, rt.RT_EULER, 1, psi0=psi0)
+    assert np.max(np.abs(psi - ref)) <= 2e-6 * np.max(np.abs(ref))
+    check_qoi(q, acc, S, 4, scale=S["mass"])
+
+
+def test_lattice_on_triangles(rt):
+    p = si.lattice_triangle_problem(28, jitter=0.2, seed=1)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 2, 16, 1, rt.RT_EULER, 20)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    bal = q["mass"] + sum(q["abs_int"]) + q["outflow_int"]
+    assert abs(bal / q["source_int"] - 1) < 1e-5
+
+
+# ------------------------------------------------------------------ BF16 storage
+def test_bf16_storage_error_is_bounded(rt):
+    """psi stored in bf16 (FP32 arithmetic): error against the FP64 oracle stays
+    at the bf16 rounding level (2^-9 relative per store), measured here."""
+    p = si.lattice_problem(70)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, 1, rt.RT_EULER, 64, dt=0.05, storage=rt.RT_BF16)
+    e = rel_l2(psi, ref)
+    assert e < 2e-2, e
+    assert rel(q["abs_int"][1], acc.abs_int[1]) < 1e-2
+    assert rel(q["mass"], S["mass"]) < 1e-2
+
+
+# ------------------------------------------------------------------ execution paths
+def test_graph_replay_matches_direct_launches_bitwise(rt):
+    p = si.lattice_problem(49)
+    quad = rt.rt_quad_product(2, 16)
+    a = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    b = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    a.step(40)               # graph path (16-step graphs) + 8 direct steps
+    for _ in range(40):
+        b.step(1)            # direct launches only
+    assert np.array_equal(a.psi(), b.psi())
+    assert a.qoi() == b.qoi() or all(np.array_equal(np.asarray(a.qoi()[k]), np.asarray(b.qoi()[k]))
+                                     for k in a.qoi())
+    a.close()
+    b.close()
+
+
+def test_checkpoint_resume_is_bitwise(rt):
+    p = si.lattice_problem(42)
+    quad = rt.rt_quad_product(2, 16)
+    a = rt.Solver(p, quad, order=1, integrator=rt.RT_EULER, dt=0.5 * p.mesh.dx)
+    a.step(11)
+    blob = rt.rt_get_state(a.h)
+    a.step(9)
+    qa, pa = a.qoi(), a.psi()
+    b = rt.Solver(p, quad, order=1, integrator=rt.RT_EULER, dt=0.5 * p.mesh.dx)
+    rt.rt_set_state(b.h, blob)
+    b.step(9)
+    qb, pb = b.qoi(), b.psi()
+    assert np.array_equal(pa, pb)
+    for k in qa:
+        assert np.array_equal(np.asarray(qa[k]), np.asarray(qb[k])), k
+    a.close()
+    b.close()
+
+
+def test_step_clamps_at_final_time(rt):
+    p = si.lattice_problem(14)
+    s = rt.Solver(p, rt.rt_quad_product(2, 4), dt=0.25)
+    s.step(1000)
+    q = s.qoi()
+    assert q["step"] == s.info.n_steps and abs(q["t"] - p.t_end) < 1e-12
+    s.close()
+
+
+def test_timeout_reports_status_and_context_survives(rt):
+    """A wait with a tiny limit on a load that is never issued: the kernel gives
+    up, reports RT_ETIMEOUT, and the GPU stays usable."""
+    p = si.lattice_problem(35)
+    quad = rt.rt_quad_product(2, 16)
+    s = rt.Solver(p, quad, dt=0.1)
+    rt.rt_debug_set(s.h, "wait_limit_cycles", 2_000_000)
+    rt.rt_debug_set(s.h, "drop_load", 3)
+    s.step(1)
+    with pytest.raises(rt.RTError) as e:
+        s.qoi()
+    assert e.value.code == rt.RT_ETIMEOUT
+    with pytest.raises(rt.RTError) as e:
+        s.step(1)
+    assert e.value.code == rt.RT_ESTATE
+    s.close()
+    # a fresh solver on the same context works
+    t = rt.Solver(p, quad, dt=0.1)
+    t.step(3)
+    assert t.qoi()["step"] == 3
+    t.close()
+
+
+def test_nonfinite_is_detected(rt):
+    p = si.lattice_problem(14)
+    p.materials.sigma_a = np.array([0.0, 3.0e38, 0.0])
+    s = rt.Solver(p, rt.rt_quad_product(2, 4), dt=0.25)
+    s.step(6)
+    with pytest.raises(rt.RTError) as e:
+        s.qoi()
+    assert e.value.code == rt.RT_ENONFINITE
+    s.close()
+
+
+def test_set_psi_roundtrip_and_device_view(rt):
+    import torch
+    p = si.lattice_problem(21)
+    s = rt.Solver(p, rt.rt_quad_product(2, 8), dt=0.1)
+    psi0 = si.random_psi(p.mesh.n_cells, 16, seed=4)
+    s.set_psi(psi0)
+    back = s.psi()
+    assert np.max(np.abs(back - psi0)) <= 1e-7 * np.max(psi0)     # FP32 rounding
+    q = s.qoi()
+    op = oracle.CartesianOracle(p, oracle.product_quadrature(2, 8))
+    assert rel(q["mass"], op.integrands(psi0)["mass"]) < 1e-6
+    ptr, phiptr, storage = rt.rt_device_state(s.h)
+    assert ptr and phiptr and storage == rt.RT_FP32
+    s.close()
+
+
+# ------------------------------------------------------------------ batches
+def test_batch_results_equal_single_solves_bitwise(rt):
+    """Mixed grid sizes and ordinate counts in one batch: each problem's result is
+    bit-identical to solving it alone (same kernels, same work split, fixed
+    reduction order)."""
+    inst = [(28, 2, 16, 8.0, 1.2), (35, 4, 16, 12.0, 0.7), (21, 2, 32, 5.5, 1.4)]
+    probs, quads = [], []
+    for n, n_p, n_phi, sa, ss in inst:
+        pr = si.lattice_problem(n, sigma_a_blue=sa, sigma_s_scatter=ss)
+        pr.t_end = 1.0
+        probs.append(pr)
+        quads.append(rt.rt_quad_product(n_p, n_phi))
+    dts = [0.5 * pr.mesh.dx for pr in probs]
+    b = rt.Batch(probs, quads, order=2, integrator=rt.RT_HEUN, dts=dts)
+    b.run()
+    for i, (pr, qd) in enumerate(zip(probs, quads)):
+        s = rt.Solver(pr, qd, order=2, integrator=rt.RT_HEUN, dt=dts[i])
+        s.step()
+        assert np.array_equal(b.psi(i), s.psi())
+        qa, qb = b.qoi(i), s.qoi()
+        assert qa["step"] == qb["step"] == s.info.n_steps
+        for k in qa:
+            assert np.array_equal(np.asarray(qa[k]), np.asarray(qb[k])), k
+        s.close()
+    b.close()
+
+
+def test_batch_against_oracle(rt):
+    probs = [si.lattice_problem(21, sigma_a_blue=7.0), si.lattice_problem(14, sigma_a_blue=13.0)]
+    for pr in probs:
+        pr.t_end = 0.8
+    quads = [rt.rt_quad_product(2, 8), rt.rt_quad_product(2, 16)]
+    b = rt.Batch(probs, quads, order=2, integrator=rt.RT_HEUN, dts=[0.5 * pr.mesh.dx for pr in probs])
+    b.run()
+    for i, pr in enumerate(probs):
+        n_p, n_phi = (2, 8) if i == 0 else (2, 16)
+        op = oracle.CartesianOracle(pr, oracle.product_quadrature(n_p, n_phi), order=2)
+        n = oracle.n_steps_for(pr.t_end, 0.5 * pr.mesh.dx)
+        ref, acc, S = oracle.run(op, np.zeros((pr.mesh.n_cells, n_p * n_phi)), pr.t_end / n, n, "heun")
+        assert rel_l2(b.psi(i), ref) <= PSI_TOL
+        check_qoi(b.qoi(i), acc, S, 3, scale=S["mass"])
+    b.close()
