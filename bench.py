@@ -36,6 +36,7 @@ WORKLOADS = {
     "lattice1400_o1_euler_fp32": ("lattice", 1400, 16, 32, 1, "euler", "fp32", 0.5, 3.2),
     "enclosure1300_tri_o1_euler_fp32": ("enclosure", 1300, 8, 32, 1, "euler", "fp32", 0.0, 2.6),
     "lattice70_o1_euler_fp32": ("lattice", 70, 4, 16, 1, "euler", "fp32", 0.5, 3.2),
+    "lattice560_muscl_heun_fp32": ("lattice", 560, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
 }
 DEFAULT = "lattice1400_muscl_heun_fp32"
 

@@ -40,7 +40,7 @@ rt_status launch_steps_direct(rt_solver* s, int64_t n, cudaStream_t stream) {
   const Instance& I = s->I;
   for (int64_t i = 0; i < n; ++i) {
     rt_status st = launch_step(s->d_desc, s->d_stage_items, (int)I.stage_items.size(), I.kind, I.integrator,
-                               I.storage, I.order, I.tx, I.ly, I.vec, stream);
+                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream);
     if (st != RT_OK) return st;
   }
   return RT_OK;
@@ -132,16 +132,7 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
     set_error("copying the solver descriptor failed: %s", cudaGetErrorString(cudaGetLastError()));
     return bail(RT_ECUDA);
   }
-  if (I.kind == RT_MESH_CARTESIAN) {
-    const int stages[2] = {I.integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
-    for (int i = 0; i < (I.integrator == RT_HEUN ? 2 : 1); ++i) {
-      cudaError_t e = prepare_cart_stage(stages[i], I.order, I.storage, I.tx, I.ly);
-      if (e != cudaSuccess) {
-        set_error("kernel set-up failed: %s", cudaGetErrorString(e));
-        return bail(RT_ECUDA);
-      }
-    }
-  }
+  if ((st = prepare_instance_kernels(I, I.ly)) != RT_OK) return bail(st);
   if ((st = run_init(s)) != RT_OK) return bail(st);
   InstState h;
   if ((st = read_state(s, &h)) != RT_OK) return bail(st);

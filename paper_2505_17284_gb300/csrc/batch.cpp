@@ -22,7 +22,7 @@ namespace {
 constexpr int kBatchGraphSteps = 8;
 
 struct Group {
-  int kind, order, tx, vec, ly_max;
+  int kind, order, run, cvec, vec, ly_max;
   int offset, count;
 };
 }  // namespace
@@ -50,7 +50,7 @@ static rt_status enqueue_phase_steps(rt_batch* b, const std::vector<Group>& grou
   for (int64_t i = 0; i < n; ++i) {
     for (const Group& g : groups) {
       rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, b->integrator, b->storage,
-                                 g.order, g.tx, g.ly_max, g.vec, stream);
+                                 g.order, g.run, g.cvec, g.ly_max, g.vec, stream);
       if (st != RT_OK) return st;
     }
   }
@@ -130,14 +130,7 @@ rt_status rt_batch_create(int32_t k, const rt_problem* problems, const rt_option
   }
   for (int i = 0; i < k; ++i) {
     const Instance& I = b->inst[i];
-    if (I.kind == RT_MESH_CARTESIAN) {
-      const int stages[2] = {I.integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
-      for (int s = 0; s < (I.integrator == RT_HEUN ? 2 : 1); ++s)
-        if (prepare_cart_stage(stages[s], I.order, I.storage, I.tx, I.ly) != cudaSuccess) {
-          set_error("kernel set-up failed");
-          return bail(RT_ECUDA);
-        }
-    }
+    if ((st = prepare_instance_kernels(I, I.ly)) != RT_OK) return bail(st);
     cudaError_t e = launch_init(b->d_desc + i, b->d_init_items + b->init_offset[i], (int)I.init_items.size(), I.vec,
                                 I.storage, b->stream);
     if (e != cudaSuccess) {
@@ -173,17 +166,17 @@ rt_status rt_batch_run(rt_batch* b, int64_t max_steps) {
       if (b->done[i] < target[i]) phase = std::min(phase, target[i] - b->done[i]);
     if (phase == INT64_MAX) break;
     // work list of the unfinished problems, grouped by kernel variant
-    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_variant;
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_variant;
     for (int i = 0; i < k; ++i) {
       if (b->done[i] >= target[i]) continue;
       const Instance& I = b->inst[i];
-      by_variant[std::make_tuple(I.kind, I.order, I.tx, I.vec)].push_back(i);
+      by_variant[std::make_tuple(I.kind, I.order, I.run, I.cvec, I.vec)].push_back(i);
     }
     std::vector<WorkItem> items;
     std::vector<Group> groups;
     for (auto& kv : by_variant) {
       Group g{};
-      std::tie(g.kind, g.order, g.tx, g.vec) = kv.first;
+      std::tie(g.kind, g.order, g.run, g.cvec, g.vec) = kv.first;
       g.offset = (int)items.size();
       g.ly_max = 1;
       for (int i : kv.second) {
@@ -196,14 +189,8 @@ rt_status rt_batch_run(rt_batch* b, int64_t max_steps) {
       }
       g.count = (int)items.size() - g.offset;
       groups.push_back(g);
-      if (g.kind == RT_MESH_CARTESIAN) {
-        const int stages[2] = {b->integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
-        for (int s = 0; s < (b->integrator == RT_HEUN ? 2 : 1); ++s)
-          if (prepare_cart_stage(stages[s], g.order, b->storage, g.tx, g.ly_max) != cudaSuccess) {
-            set_error("kernel set-up failed");
-            return batch_fail(b, RT_ECUDA);
-          }
-      }
+      rt_status pst = prepare_instance_kernels(b->inst[kv.second[0]], g.ly_max);
+      if (pst != RT_OK) return batch_fail(b, pst);
     }
     cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
                                     b->stream);

@@ -1,28 +1,35 @@
 // Cartesian stage kernel of the explicit S_N step (Sec. 4.2-4.3).
 //
-// One CTA owns a tile of TX cells in x (a strip) by `ly` rows in y (a segment)
-// and loops over the ordinate chunks of 32 ordinates (lane = ordinate). For
-// each chunk it walks the tile's rows in +y: every row (TX + 2H cells x 32
-// ordinates, H = halo = order) arrives by one TMA box load into a ring of
-// NS shared-memory slots guarded by mbarriers. When row p arrives each thread
-//   - pulls its cells' values of row p into a register window in y,
-//   - evaluates the x part of the upwind flux divergence of row p from the
-//     shared row (MUSCL-minmod or first order, boundary faces first order),
-// then the slot is released and the row p - H is completed from registers:
-//   F = -(div_x + div_y) - sigma_t psi + sigma_s/(2 pi) phi + Q   (Eq. sn_2d_eqn_fv)
-//   Euler / Heun stage 1: out = psi + dt F;  Heun stage 2: out = (psi^n + psi1 + dt F)/2
-// and stored with coalesced 128-byte rows. phi_out = sum_k w_k out_k is
-// accumulated per cell in shared memory, chunk after chunk (fixed order, no
-// atomics). The epilogue writes phi_out and the FP64 QoI partials (absorption
-// per region, mass, boundary outflow) of the output state; the last CTA of the
-// instance reduces them and applies the time-integration weights.
+// Work split. One CTA (8 warps) owns a strip of TX = 8R cells in x by a segment
+// of `ly` rows in y and loops over the ordinate chunks of C = 32V ordinates
+// (lane l holds ordinates l*V .. l*V+V-1 of the chunk, read as one vector from
+// shared memory). Warp w owns the run of R consecutive cells w*R .. w*R+R-1.
+// For each chunk the CTA walks its rows in +y: every row of (TX + 2H) cells x C
+// ordinates (H = halo = order) arrives by one TMA box load into a ring of shared
+// memory slots guarded by mbarriers; a row stays resident until it has been
+// completed (H rows after its arrival), then its slot takes the next load.
 //
-// Upwind coordinates: for an ordinate with direction sign d along an axis the
-// stencil is u2 = psi_{i-2d}, u1 = psi_{i-d}, c = psi_i, d1 = psi_{i+d}; the
-// outgoing face carries c + minmod(d1 - c, c - u1)/2 and the incoming face
-// u1 + minmod(c - u1, u1 - u2)/2, so div = |v|/h (F_out - F_in). Cells beyond
-// the domain hold the ghost value psi^- of that side (Sec. 4.2); faces on the
-// boundary are first order.
+// Fluxes. Each face value is computed once (Eq. upwind1stOrder with R =
+// psi +/- slope/2, minmod slopes per dimension):
+//   x: the lane reads its run in upwind order (addresses step by the sign d of
+//      xi), so face m (outgoing face of the m-th cell along the flow) is
+//      u_m + h_m minmod(u_{m+1} - u_m, u_m - u_{m-1}) and the divergence of cell
+//      m is |xi|/dx (F_m - F_{m-1});
+//   y: a register window over the rows gives the face j+1/2 once per row, from
+//      the upwind cell (j if eta > 0, j+1 if eta < 0), and the divergence of row j
+//      is eta/dy (G_{j+1/2} - G_{j-1/2}).
+// minmod(a, b) is the median of (a, b, 0). h = 1/2 except on domain boundary
+// faces, which are first order (h = 0). Cells outside the domain hold the side's
+// ghost value psi^- (Sec. 4.2); only CTAs touching the boundary take that path.
+//
+// Update. With a = 1 - dt sigma_t and b = dt (sigma_s/(2 pi) phi + Q) per cell:
+//   Euler / Heun stage 1: out = a psi + b - dt (div_x + div_y)
+//   Heun stage 2:         out = (psi^n + a psi1 + b - dt (div_x + div_y)) / 2
+// (Eq. sn_2d_eqn_fv and Sec. 4.3). phi_out = sum_k w_k out_k is accumulated per
+// cell in shared memory chunk after chunk (fixed order). The epilogue writes
+// phi_out and FP64 QoI partials (absorption per region, mass, boundary outflow)
+// of the output state; the last CTA of the instance reduces them in order and
+// applies the time-integration weights.
 #include <cuda_bf16.h>
 
 #include "device_common.cuh"
@@ -31,41 +38,101 @@ namespace rtk {
 
 constexpr int kCartThreads = 256;
 constexpr int kCartWarps = kCartThreads / 32;
-constexpr int kSlots = 6;
 
-template <int H, int TX, int STAGE, typename T>
-struct CartLayout {
-  static constexpr int halo_bytes = (TX + 2 * H) * kChunk * (int)sizeof(T);
-  static constexpr int base_bytes = (STAGE == STAGE_HEUN2) ? TX * kChunk * (int)sizeof(T) : 0;
-  static constexpr int slot_bytes = ((halo_bytes + base_bytes) + 127) / 128 * 128;
-  static constexpr int ring_bytes = kSlots * slot_bytes;
+template <int ORDER, int R, int V, int STAGE, typename T>
+struct CartCfg {
+  static constexpr int H = ORDER;                 // halo cells in x and rows in y
+  static constexpr int TX = kCartWarps * R;       // cells per strip
+  static constexpr int C = 32 * V;                // ordinates per chunk
+  static constexpr int NS = (STAGE == STAGE_HEUN2) ? 5 : 6;   // ring slots
+  static constexpr int halo_bytes = (TX + 2 * H) * C * (int)sizeof(T);
+  static constexpr int base_bytes = (STAGE == STAGE_HEUN2) ? TX * C * (int)sizeof(T) : 0;
+  static constexpr int slot_bytes = (halo_bytes + base_bytes + 127) / 128 * 128;
+  static constexpr int ring_bytes = NS * slot_bytes;
+  static constexpr int NL = R + 2 * H - 1;        // values read per row: m = -H .. R+H-2
 };
 
 __host__ __device__ inline size_t cart_tile_bytes(int tx, int ly) {
-  // phi_in [ly][tx] float, phi_acc [ly][tx] float, mat [ly][tx] uint8 (padded)
-  return (size_t)ly * tx * 8 + (((size_t)ly * tx + 127) / 128 * 128);
+  // a [ly][tx], b [ly][tx], phi_acc [ly][tx] (float)
+  return ((size_t)ly * tx * 12 + 127) / 128 * 128;
 }
 
-// barriers (128) + FP64 reduction rows ((warps + 1) x NQ) + material table + alignment slack
+// barriers (128) + FP64 reduction rows ((warps + 1) x NQ) + alignment slack
 constexpr size_t kCartRedBytes = (kCartWarps + 1) * NQ * 8;
-constexpr size_t kCartFixedBytes = 128 + kCartRedBytes + 3 * kMaxMat * 4 + 128;
+constexpr size_t kCartFixedBytes = 128 + kCartRedBytes + 128;
 
-template <int ORDER, int TX, int STAGE, typename T>
-__global__ void __launch_bounds__(kCartThreads)
-    cart_stage_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
-  constexpr int H = ORDER;
-  constexpr int CPW = TX / kCartWarps;   // cells per warp in a row
-  constexpr int WIN = 2 * H + 1;         // y window: rows j-H .. j+H
-  using L = CartLayout<H, TX, STAGE, T>;
-  static_assert(CPW == 4 || CPW == 8, "TX must be 32 or 64");
+template <int ORDER, int R, int V, int STAGE, typename T>
+size_t cart_smem_for(int ly) {
+  using L = CartCfg<ORDER, R, V, STAGE, T>;
+  return L::ring_bytes + cart_tile_bytes(L::TX, ly) + kCartFixedBytes;
+}
 
-  const WorkItem it = items[blockIdx.x];
-  const InstDesc& d = descs[it.inst];
-  InstState* st = d.st;
-  // finished or failed instances are masked
-  if (st->step >= d.n_steps || st->status != DEV_OK) return;
+// minmod(a, b) = median(a, b, 0): 0 unless a and b share a sign, else the one of
+// smaller magnitude.
+__device__ __forceinline__ float minmod_med(float a, float b) {
+  const float lo = fminf(a, b), hi = fmaxf(a, b);
+  return fmaxf(lo, fminf(hi, 0.f));
+}
 
+template <typename T, int V>
+__device__ __forceinline__ void lds_vec(const T* p, float (&out)[V]) {
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (V == 4) {
+      const float4 x = *reinterpret_cast<const float4*>(p);
+      out[0] = x.x; out[1] = x.y; out[2] = x.z; out[3] = x.w;
+    } else if constexpr (V == 2) {
+      const float2 x = *reinterpret_cast<const float2*>(p);
+      out[0] = x.x; out[1] = x.y;
+    } else {
+      out[0] = *reinterpret_cast<const float*>(p);
+    }
+  } else {
+    if constexpr (V == 4) {
+      const uint2 x = *reinterpret_cast<const uint2*>(p);
+      const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x.x));
+      const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x.y));
+      out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
+    } else if constexpr (V == 2) {
+      const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+      out[0] = fa.x; out[1] = fa.y;
+    } else {
+      out[0] = __bfloat162float(*p);
+    }
+  }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stg_vec(T* p, const float (&in)[V]) {
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (V == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(in[0], in[1], in[2], in[3]);
+    } else if constexpr (V == 2) {
+      *reinterpret_cast<float2*>(p) = make_float2(in[0], in[1]);
+    } else {
+      *reinterpret_cast<float*>(p) = in[0];
+    }
+  } else {
+    if constexpr (V == 4) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(in[0], in[1]);
+      __nv_bfloat162 b = __floats2bfloat162_rn(in[2], in[3]);
+      uint2 x;
+      x.x = *reinterpret_cast<uint32_t*>(&a);
+      x.y = *reinterpret_cast<uint32_t*>(&b);
+      *reinterpret_cast<uint2*>(p) = x;
+    } else if constexpr (V == 2) {
+      *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(in[0], in[1]);
+    } else {
+      *p = __float2bfloat16_rn(in[0]);
+    }
+  }
+}
+
+template <int ORDER, int R, int V, int STAGE, typename T, bool XB, bool YB>
+__device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it, InstState* st, uint8_t* smem) {
+  using L = CartCfg<ORDER, R, V, STAGE, T>;
+  constexpr int H = L::H, TX = L::TX, C = L::C, NS = L::NS, NL = L::NL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
   const int parity = (STAGE == STAGE_EULER) ? st->parity : 0;
   const int in_buf = (STAGE == STAGE_EULER) ? parity : (STAGE == STAGE_HEUN1 ? 0 : 1);
   const int out_buf = (STAGE == STAGE_EULER) ? (1 - parity) : (STAGE == STAGE_HEUN1 ? 1 : 0);
@@ -80,25 +147,19 @@ __global__ void __launch_bounds__(kCartThreads)
   const int ya = it.b * d.ly;
   const int yb = min(ny, ya + d.ly);
   const int nrows = yb - ya;
-  const int Lc = nrows + 2 * H;                 // pulled rows per chunk: ya-H .. yb+H-1
+  const int Lc = nrows + 2 * H;     // rows pulled per chunk: ya-H .. yb+H-1
   const int total = d.n_chunks * Lc;
 
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  // TMA destinations want 128-byte alignment; the launch adds 128 bytes of slack
-  uint8_t* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint8_t* ring = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::ring_bytes);            // kSlots + 1
-  float* tile_phi = reinterpret_cast<float*>(smem + L::ring_bytes + 128);         // [ly][TX]
-  float* tile_acc = tile_phi + d.ly * TX;                                           // [ly][TX]
-  uint8_t* tile_mat = reinterpret_cast<uint8_t*>(tile_acc + d.ly * TX);            // [ly][TX]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::ring_bytes);
+  float* tile_a = reinterpret_cast<float*>(smem + L::ring_bytes + 128);
+  float* tile_b = tile_a + d.ly * TX;
+  float* tile_acc = tile_b + d.ly * TX;
   double* red = reinterpret_cast<double*>(smem + L::ring_bytes + 128 + cart_tile_bytes(TX, d.ly));
-  float* mtab = reinterpret_cast<float*>(red + (kCartWarps + 1) * NQ);              // sig_t, sig_s2pi, q
-
   const int64_t limit = d.wait_limit;
 
-  // ---- producer: issue the loads of sequence entry q into slot q % kSlots
   auto issue = [&](int q) {
-    const int slot = q % kSlots;
+    const int slot = q % NS;
     const int c = q / Lc;
     const int p = ya - H + (q - c * Lc);
     uint8_t* dst = ring + slot * L::slot_bytes;
@@ -111,12 +172,12 @@ __global__ void __launch_bounds__(kCartThreads)
       return;
     }
     mbar_arrive_expect_tx(&bars[slot], bytes);
-    if (halo) tma_load_3d(dst, map_halo, &bars[slot], c * kChunk, x0 - H, p);
-    if (base) tma_load_3d(dst + L::halo_bytes, map_base, &bars[slot], c * kChunk, x0, p - H);
+    if (halo) tma_load_3d(dst, map_halo, &bars[slot], c * C, x0 - H, p);
+    if (base) tma_load_3d(dst + L::halo_bytes, map_base, &bars[slot], c * C, x0, p - H);
   };
 
   if (tid == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
     fence_tensormap_acquire(map_halo);
     prefetch_tensormap(map_halo);
@@ -127,178 +188,224 @@ __global__ void __launch_bounds__(kCartThreads)
   }
   __syncthreads();
   if (tid == 0) {
-    for (int q = 0; q < min(kSlots, total); ++q) issue(q);
+    for (int q = 0; q < min(NS, total); ++q) issue(q);
   }
-  // ---- tile constants: phi of the stage input, material ids, material table
+  // per-cell constants of the tile: a = 1 - dt sigma_t, b = dt (sigma_s/(2 pi) phi + Q)
+  const float dt = d.dt;
   for (int i = tid; i < nrows * TX; i += kCartThreads) {
     const int r = i / TX, xl = i - r * TX;
     const int gx = x0 + xl;
-    const size_t cell = (size_t)(ya + r) * nx + gx;
-    const bool in = gx < nx;
-    tile_phi[i] = in ? phi_in[cell] : 0.f;
-    tile_mat[i] = in ? d.mat[cell] : 0;
+    float a = 1.f, b = 0.f;
+    if (gx < nx) {
+      const size_t cell = (size_t)(ya + r) * nx + gx;
+      const int m = d.mat[cell];
+      a = 1.f - dt * d.sig_t[m];
+      b = dt * (d.sig_s2pi[m] * phi_in[cell] + d.q_src[m]);
+    }
+    tile_a[i] = a;
+    tile_b[i] = b;
     tile_acc[i] = 0.f;
-  }
-  if (tid < kMaxMat) {
-    mtab[tid] = d.sig_t[tid];
-    mtab[kMaxMat + tid] = d.sig_s2pi[tid];
-    mtab[2 * kMaxMat + tid] = d.q_src[tid];
   }
   __syncthreads();
 
-  const float dt = d.dt;
-  double bacc = 0.0;   // boundary outflow of the output state (this thread's terms)
+  float bacc = 0.f;   // boundary outflow terms of this thread (FP32; FP64 from the block reduction on)
+  const float ly_f = (float)d.dy_d, lx_f = (float)d.dx_d;
+  const int xl0 = warp * R;   // first cell of this thread's run (tile-local)
+  static_assert(NS >= H + 2, "the ring must hold the resident rows plus one load in flight");
 
-  int q = 0;          // next sequence entry to consume
-  int issued = min(kSlots, total);
+  int q = 0;
+  int issued = min(NS, total);
   for (int c = 0; c < d.n_chunks; ++c) {
-    const int k = c * kChunk + lane;
-    const float xi = d.xi[k], eta = d.eta[k], wk = d.w[k];
-    const int dxs = (xi > 0.f) ? 1 : -1;
-    const int dys = (eta > 0.f) ? 1 : -1;
-    const float ax = fabsf(xi) * d.inv_dx, ay = fabsf(eta) * d.inv_dy;
-    // psi^- of each side for this ordinate: the inflow value if it enters there, else 0
-    const float g_xlo = (xi > 0.f) ? d.ghost[0] : 0.f;
-    const float g_xhi = (xi < 0.f) ? d.ghost[1] : 0.f;
-    const float g_ylo = (eta > 0.f) ? d.ghost[2] : 0.f;
-    const float g_yhi = (eta < 0.f) ? d.ghost[3] : 0.f;
-    const float gx_up = (dxs > 0) ? g_xlo : g_xhi;   // ghost on the upwind side in x
-    const float gy_up = (dys > 0) ? g_ylo : g_yhi;
-
-    float win[CPW][WIN];     // psi at rows j-H..j+H for each cell of this thread
-    float dxw[CPW][H + 1];   // x divergence at rows j..j+H
+    const int k0 = c * C + lane * V;
+    float w[V], ax[V], ay[V], eneg[V];
+    float xsum = 0.f;
 #pragma unroll
-    for (int u = 0; u < CPW; ++u) {
-#pragma unroll
-      for (int r = 0; r < WIN; ++r) win[u][r] = 0.f;
-#pragma unroll
-      for (int r = 0; r <= H; ++r) dxw[u][r] = 0.f;
+    for (int v = 0; v < V; ++v) {
+      const float xiv = d.xi[k0 + v], etav = d.eta[k0 + v];
+      w[v] = d.w[k0 + v];
+      xsum += xiv;
+      ax[v] = dt * fabsf(xiv) * d.inv_dx;
+      ay[v] = dt * etav * d.inv_dy;
+      eneg[v] = (etav < 0.f) ? 1.f : 0.f;
     }
+    const int dxs = (xsum >= 0.f) ? 1 : -1;    // lane's flow direction in x (uniform over its V ordinates)
+    const int s0 = (dxs > 0) ? xl0 : xl0 + R - 1;
+    // register window over rows (carried between pulls): c1 = row p-1, c2 = row p-2,
+    // dprev = c_{p-2} - c_{p-3}, gprev = face value below the row being completed
+    float c1[R][V], c2[R][V], dprev[R][V], gprev[R][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int v = 0; v < V; ++v) c1[r][v] = c2[r][v] = dprev[r][v] = gprev[r][v] = 0.f;
 
     for (int p = ya - H; p < yb + H; ++p, ++q) {
-      const int slot = q % kSlots;
-      const uint32_t par = (uint32_t)((q / kSlots) & 1);
-      const uint8_t* sl = ring + slot * L::slot_bytes;
-      const T* srow = reinterpret_cast<const T*>(sl);
-      const T* sbase = reinterpret_cast<const T*>(sl + L::halo_bytes);
+      const int slot = q % NS;
+      const uint32_t par = (uint32_t)((q / NS) & 1);
       const bool ok = mbar_wait_bounded(&bars[slot], par, limit);
-      const bool p_in = (p >= 0 && p < ny);
-      const bool p_tile = (p >= ya && p < yb);
-      float vnew[CPW], dnew[CPW], bse[CPW];
+      const T* srow = reinterpret_cast<const T*>(ring + slot * L::slot_bytes);
+      // ---- the new row p: own cells, in upwind order
+      float c0[R][V];
+      if (YB && (p < 0 || p >= ny)) {
 #pragma unroll
-      for (int u = 0; u < CPW; ++u) {
-        const int xl = warp + kCartWarps * u;
-        const int xs = xl + H;
-        const int gx = x0 + xl;
-        float cv = p_in ? Store<T>::from_smem(srow[xs * kChunk + lane]) : (p < 0 ? g_ylo : g_yhi);
-        vnew[u] = cv;
-        float dv = 0.f;
-        if (p_tile) {
-          const float u1 = Store<T>::from_smem(srow[(xs - dxs) * kChunk + lane]);
-          const bool in_bnd = (gx - dxs < 0) || (gx - dxs >= nx);
-          const bool out_bnd = (gx + dxs < 0) || (gx + dxs >= nx);
-          if constexpr (ORDER == 1) {
-            const float f_in = in_bnd ? gx_up : u1;
-            dv = ax * (cv - f_in);
-          } else {
-            const float u2 = Store<T>::from_smem(srow[(xs - 2 * dxs) * kChunk + lane]);
-            const float d1 = Store<T>::from_smem(srow[(xs + dxs) * kChunk + lane]);
-            const bool u2_out = (gx - 2 * dxs < 0) || (gx - 2 * dxs >= nx);
-            const float u1v = in_bnd ? gx_up : u1;
-            const float u2v = (in_bnd || u2_out) ? gx_up : u2;
-            const float f_in = in_bnd ? gx_up : u1 + 0.5f * minmod(cv - u1, u1 - u2v);
-            const float f_out = out_bnd ? cv : cv + 0.5f * minmod(d1 - cv, cv - u1v);
-            dv = ax * (f_out - f_in);
+        for (int v = 0; v < V; ++v) {
+          const float etav = d.eta[k0 + v];
+          const float gv = (p < 0) ? ((etav > 0.f) ? d.ghost[2] : 0.f) : ((etav < 0.f) ? d.ghost[3] : 0.f);
+#pragma unroll
+          for (int r = 0; r < R; ++r) c0[r][v] = gv;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) lds_vec<T, V>(srow + (s0 + dxs * r + H) * C + lane * V, c0[r]);
+        if constexpr (XB) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int g = x0 + s0 + dxs * r;
+            if (g >= nx) {   // ragged tile: cells beyond the domain (never stored)
+#pragma unroll
+              for (int v = 0; v < V; ++v) c0[r][v] = 0.f;
+            }
           }
         }
-        dnew[u] = dv;
-        bse[u] = 0.f;
-        if constexpr (STAGE == STAGE_HEUN2) {
-          if (p - H >= ya) bse[u] = Store<T>::from_smem(sbase[xl * kChunk + lane]);
-        }
       }
-      // all reads of the slot are done (or the wait ran out)
+      // ---- y face f + 1/2 with f = p - H, from the upwind cell of the face
+      const int f = p - H;
+      const bool do_face = (f >= ya - 1);
+      float g[R][V];
+      if constexpr (ORDER == 2) {
+        float hmul = 0.5f;
+        if constexpr (YB) hmul = (f == -1 || f == ny - 1) ? 0.f : 0.5f;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float db = c1[r][v] - c2[r][v];        // c_{f+1} - c_f
+            const float dcv = c0[r][v] - c1[r][v];       // c_{f+2} - c_{f+1}
+            const float qv = (eneg[v] != 0.f) ? dcv : dprev[r][v];
+            const float gf = fmaf(eneg[v], db, c2[r][v]);
+            const float hv = (eneg[v] != 0.f) ? -hmul : hmul;
+            g[r][v] = do_face ? fmaf(hv, minmod_med(db, qv), gf) : gf;
+            dprev[r][v] = db;
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int v = 0; v < V; ++v) g[r][v] = fmaf(eneg[v], c0[r][v] - c1[r][v], c1[r][v]);
+      }
+      // ---- completion of row j = p - H (its slot, entry q - H, is still resident)
+      const int j = p - H;
+      if (j >= ya) {
+        const T* jrow = reinterpret_cast<const T*>(ring + ((q - H) % NS) * L::slot_bytes);
+        const T* sbase = reinterpret_cast<const T*>(ring + slot * L::slot_bytes + L::halo_bytes);
+        const int rr = j - ya;
+        float u[NL][V];
+#pragma unroll
+        for (int m = 0; m < NL; ++m) {
+          const int pos = s0 + dxs * (m - H);   // tile-local cell of upwind index m - H
+          lds_vec<T, V>(jrow + (pos + H) * C + lane * V, u[m]);
+          if constexpr (XB) {
+            const int gpos = x0 + pos;
+            if (gpos < 0 || gpos >= nx) {
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                const float xiv = d.xi[k0 + v];
+                u[m][v] = (gpos < 0) ? ((xiv > 0.f) ? d.ghost[0] : 0.f) : ((xiv < 0.f) ? d.ghost[1] : 0.f);
+              }
+            }
+          }
+        }
+        // faces m = -1 .. R-1 along x (outgoing face of upwind cell m); first order on domain faces
+        float F[R + 1][V];
+#pragma unroll
+        for (int m = -1; m < R; ++m) {
+          float h = (ORDER == 2) ? 0.5f : 0.f;
+          if constexpr (XB) {
+            const int ga = x0 + s0 + dxs * m, gb = ga + dxs;
+            if (!((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) h = 0.f;
+          }
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float um = u[m + H][v];
+            if constexpr (ORDER == 2) {
+              const float dn = u[m + H + 1][v] - um, up = um - u[m + H - 1][v];
+              F[m + 1][v] = fmaf(h, minmod_med(dn, up), um);
+            } else {
+              F[m + 1][v] = um;
+            }
+          }
+        }
+        float contrib[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int xl = s0 + dxs * r;
+          const int gx = x0 + xl;
+          const float ta = tile_a[rr * TX + xl], tb = tile_b[rr * TX + xl];
+          float bse[V];
+          if constexpr (STAGE == STAGE_HEUN2) lds_vec<T, V>(sbase + xl * C + lane * V, bse);
+          const float(&cj)[V] = (ORDER == 2) ? c2[r] : c1[r];
+          float out[V];
+          float pw = 0.f;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float dxv = ax[v] * (F[r + 1][v] - F[r][v]);
+            const float div = fmaf(ay[v], g[r][v] - gprev[r][v], dxv);
+            float t = fmaf(ta, cj[v], tb) - div;
+            if constexpr (STAGE == STAGE_HEUN2) t = 0.5f * (bse[v] + t);
+            t = Store<T>::round(t);
+            out[v] = t;
+            pw = fmaf(w[v], t, pw);
+          }
+          contrib[r] = 0.f;
+          if (!XB || gx < nx) {
+            stg_vec<T, V>(psi_out + ((size_t)j * nx + gx) * Mpad + k0, out);
+            contrib[r] = pw;
+            if constexpr (XB || YB) {
+              // boundary outflow of the output state (first-order traces)
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                const float o = out[v], xiv = d.xi[k0 + v], etav = d.eta[k0 + v];
+                if (XB && gx == 0) bacc += ly_f * (w[v] * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
+                if (XB && gx == nx - 1) bacc += ly_f * (w[v] * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
+                if (YB && j == 0) bacc += lx_f * (w[v] * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
+                if (YB && j == ny - 1) bacc += lx_f * (w[v] * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
+              }
+            }
+          }
+        }
+        // phi partials in physical cell order, summed over the 32 lanes
+        float phys[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) phys[r] = (dxs > 0) ? contrib[r] : contrib[R - 1 - r];
+        const float sphi = multi_warp_sum<R>(phys, lane);
+        if ((lane & (32 / R - 1)) == 0) tile_acc[rr * TX + xl0 + lane / (32 / R)] += sphi;
+      }
+      // every read of entry q - H (and of this row) is done, or a wait ran out
       if (__syncthreads_or(!ok)) {
         if (tid == 0) {
-          // wait (bounded) for loads still in flight into this CTA's slots
           for (int qq = q; qq < issued; ++qq) {
             if ((int64_t)qq == d.drop_load) continue;
-            mbar_wait_bounded(&bars[qq % kSlots], (uint32_t)((qq / kSlots) & 1), limit);
+            mbar_wait_bounded(&bars[qq % NS], (uint32_t)((qq / NS) & 1), limit);
           }
           atomicCAS(&st->status, DEV_OK, DEV_TIMEOUT);
           st->timeout_where = ((int64_t)blockIdx.x << 32) | (int64_t)q;
         }
         return;
       }
-      if (tid == 0 && issued < total) {
+      // entry q - H is consumed: its slot takes entry q - H + NS
+      if (tid == 0 && q >= H && issued < total) {
         fence_proxy_async_smem();
         issue(issued);
         ++issued;
       }
-      // shift the windows
+      // shift the window
 #pragma unroll
-      for (int u = 0; u < CPW; ++u) {
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int r = 0; r < WIN - 1; ++r) win[u][r] = win[u][r + 1];
-        win[u][WIN - 1] = vnew[u];
-#pragma unroll
-        for (int r = 0; r < H; ++r) dxw[u][r] = dxw[u][r + 1];
-        dxw[u][H] = dnew[u];
-      }
-      const int j = p - H;
-      if (j < ya) continue;
-      // ---- complete row j
-      const bool yin_bnd = (j - dys < 0) || (j - dys >= ny);
-      const bool yout_bnd = (j + dys < 0) || (j + dys >= ny);
-      const bool yu2_out = (j - 2 * dys < 0) || (j - 2 * dys >= ny);
-      const int r = j - ya;
-      float contrib[CPW];
-#pragma unroll
-      for (int u = 0; u < CPW; ++u) {
-        const int xl = warp + kCartWarps * u;
-        const int gx = x0 + xl;
-        const float cv = win[u][H];
-        float dy;
-        if constexpr (ORDER == 1) {
-          const float u1 = (dys > 0) ? win[u][0] : win[u][2];
-          const float f_in = yin_bnd ? gy_up : u1;
-          dy = ay * (cv - f_in);
-        } else {
-          const float u1 = (dys > 0) ? win[u][1] : win[u][3];
-          const float u2 = (dys > 0) ? win[u][0] : win[u][4];
-          const float d1 = (dys > 0) ? win[u][3] : win[u][1];
-          const float u1v = yin_bnd ? gy_up : u1;
-          const float u2v = (yin_bnd || yu2_out) ? gy_up : u2;
-          const float f_in = yin_bnd ? gy_up : u1 + 0.5f * minmod(cv - u1, u1 - u2v);
-          const float f_out = yout_bnd ? cv : cv + 0.5f * minmod(d1 - cv, cv - u1v);
-          dy = ay * (f_out - f_in);
+        for (int v = 0; v < V; ++v) {
+          gprev[r][v] = g[r][v];
+          c2[r][v] = c1[r][v];
+          c1[r][v] = c0[r][v];
         }
-        const int ti = r * TX + xl;
-        const int m = tile_mat[ti];
-        const float F = -(dxw[u][0] + dy) - mtab[m] * cv + mtab[kMaxMat + m] * tile_phi[ti] + mtab[2 * kMaxMat + m];
-        float outv;
-        if constexpr (STAGE == STAGE_HEUN2) {
-          outv = 0.5f * (bse[u] + cv + dt * F);
-        } else {
-          outv = cv + dt * F;
-        }
-        outv = Store<T>::round(outv);
-        contrib[u] = 0.f;
-        if (gx < nx) {
-          Store<T>::store(psi_out + ((size_t)j * nx + gx) * Mpad + k, outv);
-          contrib[u] = wk * outv;
-          // boundary outflow of the output state: first-order traces
-          if (gx == 0) bacc += (double)(d.dy_d * (double)(wk * -xi * (xi < 0.f ? outv : g_xlo)));
-          if (gx == nx - 1) bacc += (double)(d.dy_d * (double)(wk * xi * (xi > 0.f ? outv : g_xhi)));
-          if (j == 0) bacc += (double)(d.dx_d * (double)(wk * -eta * (eta < 0.f ? outv : g_ylo)));
-          if (j == ny - 1) bacc += (double)(d.dx_d * (double)(wk * eta * (eta > 0.f ? outv : g_yhi)));
-        }
-      }
-      const float s = multi_warp_sum<CPW>(contrib, lane);
-      if ((lane & (32 / CPW - 1)) == 0) {
-        const int u = lane / (32 / CPW);
-        tile_acc[r * TX + warp + kCartWarps * u] += s;
-      }
     }
   }
   __syncthreads();
@@ -317,7 +424,7 @@ __global__ void __launch_bounds__(kCartThreads)
     const float ph = tile_acc[i];
     phi_out[cell] = ph;
     const int reg = d.region[cell];
-    const float va = (float)d.sig_a[tile_mat[i]] * ph;
+    const float va = d.sig_a_f[d.mat[cell]] * ph;
 #pragma unroll
     for (int g = 0; g < kMaxReg; ++g)
       if (g == reg) fa[g] += va;
@@ -329,30 +436,48 @@ __global__ void __launch_bounds__(kCartThreads)
 #pragma unroll
   for (int g = 0; g < kMaxReg; ++g)
     if (g < nreg) acc[g] = (double)fa[g] * d.area_d;
-  // compact layout for the reduction: regions, mass, outflow
 #pragma unroll
   for (int g = 0; g < kMaxReg + 1; ++g)
     if (g == nreg) acc[g] = (double)fm * d.area_d;
 #pragma unroll
   for (int g = 0; g < kMaxReg + 2; ++g)
-    if (g == nreg + 1) acc[g] = bacc;
+    if (g == nreg + 1) acc[g] = (double)bacc;
   block_reduce_q<kCartThreads>(acc, nreg + 2, red);
   finalize_item<kCartThreads>(d, it, red, STAGE, red + NQ);
 }
 
-template <int H, int TX, int STAGE, typename T>
-static size_t smem_for(int ly) {
-  using L = CartLayout<H, TX, STAGE, T>;
-  return L::ring_bytes + cart_tile_bytes(TX, ly) + kCartFixedBytes;
+template <int ORDER, int R, int V, int STAGE, typename T>
+__global__ void __launch_bounds__(kCartThreads, 2)
+    cart_stage_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
+  using L = CartCfg<ORDER, R, V, STAGE, T>;
+  const WorkItem it = items[blockIdx.x];
+  const InstDesc& d = descs[it.inst];
+  InstState* st = d.st;
+  // finished or failed instances are masked
+  if (st->step >= d.n_steps || st->status != DEV_OK) return;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  // TMA destinations want 128-byte alignment; the launch adds 128 bytes of slack
+  uint8_t* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int x0 = it.a * L::TX;
+  const int ya = it.b * d.ly;
+  const bool xb = (x0 - L::H < 0) || (x0 + L::TX + L::H > d.nx);
+  const bool yb = (ya - L::H < 0) || (ya + d.ly + L::H > d.ny);
+  if (xb) {
+    if (yb) cart_tile<ORDER, R, V, STAGE, T, true, true>(d, it, st, smem);
+    else cart_tile<ORDER, R, V, STAGE, T, true, false>(d, it, st, smem);
+  } else {
+    if (yb) cart_tile<ORDER, R, V, STAGE, T, false, true>(d, it, st, smem);
+    else cart_tile<ORDER, R, V, STAGE, T, false, false>(d, it, st, smem);
+  }
 }
 
-template <int H, int TX, int STAGE, typename T>
+template <int ORDER, int R, int V, int STAGE, typename T>
 static cudaError_t prepare_one(int ly_max) {
   // raise the dynamic shared-memory limit of this kernel variant (idempotent)
   static size_t s_limit = 0;
-  const size_t smem = smem_for<H, TX, STAGE, T>(ly_max);
+  const size_t smem = cart_smem_for<ORDER, R, V, STAGE, T>(ly_max);
   if (smem > s_limit) {
-    cudaError_t e = cudaFuncSetAttribute(cart_stage_kernel<H, TX, STAGE, T>,
+    cudaError_t e = cudaFuncSetAttribute(cart_stage_kernel<ORDER, R, V, STAGE, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     s_limit = smem;
@@ -360,43 +485,56 @@ static cudaError_t prepare_one(int ly_max) {
   return cudaSuccess;
 }
 
-template <int H, int TX, int STAGE, typename T>
+template <int ORDER, int R, int V, int STAGE, typename T>
 static cudaError_t launch_one(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int ly_max,
                               cudaStream_t stream) {
-  cudaError_t e = prepare_one<H, TX, STAGE, T>(ly_max);
+  cudaError_t e = prepare_one<ORDER, R, V, STAGE, T>(ly_max);
   if (e != cudaSuccess) return e;
-  cart_stage_kernel<H, TX, STAGE, T><<<n_items, kCartThreads, smem_for<H, TX, STAGE, T>(ly_max), stream>>>(
-      d_desc, d_items);
+  cart_stage_kernel<ORDER, R, V, STAGE, T>
+      <<<n_items, kCartThreads, cart_smem_for<ORDER, R, V, STAGE, T>(ly_max), stream>>>(d_desc, d_items);
   return cudaGetLastError();
 }
 
-#define RTK_CART_VARIANTS(X, TT)                                                             \
-  X(1, 32, STAGE_EULER, TT) X(1, 32, STAGE_HEUN1, TT) X(1, 32, STAGE_HEUN2, TT)              \
-  X(2, 32, STAGE_EULER, TT) X(2, 32, STAGE_HEUN1, TT) X(2, 32, STAGE_HEUN2, TT)              \
-  X(1, 64, STAGE_EULER, TT) X(1, 64, STAGE_HEUN1, TT) X(1, 64, STAGE_HEUN2, TT)              \
-  X(2, 64, STAGE_EULER, TT) X(2, 64, STAGE_HEUN1, TT) X(2, 64, STAGE_HEUN2, TT)
+// Variants: order {1, 2} x run length R {2, 4} x ordinates per lane V x stage.
+#define RTK_CART_STAGES(X, O, RR, VV, TT) \
+  X(O, RR, VV, STAGE_EULER, TT) X(O, RR, VV, STAGE_HEUN1, TT) X(O, RR, VV, STAGE_HEUN2, TT)
+#define RTK_CART_VARIANTS(X, TT)                                                                           \
+  RTK_CART_STAGES(X, 1, 2, 1, TT) RTK_CART_STAGES(X, 1, 2, 2, TT) RTK_CART_STAGES(X, 1, 2, 4, TT)           \
+  RTK_CART_STAGES(X, 2, 2, 1, TT) RTK_CART_STAGES(X, 2, 2, 2, TT) RTK_CART_STAGES(X, 2, 2, 4, TT)           \
+  RTK_CART_STAGES(X, 1, 4, 1, TT) RTK_CART_STAGES(X, 1, 4, 2, TT) RTK_CART_STAGES(X, 2, 4, 1, TT)           \
+  RTK_CART_STAGES(X, 2, 4, 2, TT)
 
-cudaError_t prepare_cart_stage(int stage, int order, int storage, int tx, int ly_max) {
-#define RTK_P(H, TXV, ST, TT) \
-  if (order == H && tx == TXV && stage == ST) return prepare_one<H, TXV, ST, TT>(ly_max);
+int cart_tile_width(int run) { return kCartWarps * run; }
+
+bool cart_variant_exists(int order, int run, int vec) {
+  if (order != 1 && order != 2) return false;
+  if (run == 2) return vec == 1 || vec == 2 || vec == 4;
+  if (run == 4) return vec == 1 || vec == 2;
+  return false;
+}
+
+cudaError_t prepare_cart_stage(int stage, int order, int storage, int run, int vec, int ly_max) {
+#define RTK_P(O, RR, VV, ST, TT) \
+  if (order == O && run == RR && vec == VV && stage == ST) return prepare_one<O, RR, VV, ST, TT>(ly_max);
   if (storage == 0) { RTK_CART_VARIANTS(RTK_P, float) } else { RTK_CART_VARIANTS(RTK_P, __nv_bfloat16) }
 #undef RTK_P
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_cart_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage, int order,
-                              int storage, int tx, int ly_max, cudaStream_t stream) {
+                              int storage, int run, int vec, int ly_max, cudaStream_t stream) {
   if (n_items <= 0) return cudaSuccess;
-#define RTK_L(H, TXV, ST, TT) \
-  if (order == H && tx == TXV && stage == ST) return launch_one<H, TXV, ST, TT>(d_desc, d_items, n_items, ly_max, stream);
+#define RTK_L(O, RR, VV, ST, TT)                              \
+  if (order == O && run == RR && vec == VV && stage == ST) \
+    return launch_one<O, RR, VV, ST, TT>(d_desc, d_items, n_items, ly_max, stream);
   if (storage == 0) { RTK_CART_VARIANTS(RTK_L, float) } else { RTK_CART_VARIANTS(RTK_L, __nv_bfloat16) }
 #undef RTK_L
   return cudaErrorInvalidValue;
 }
 
-size_t cart_smem_bytes(int order, int storage, int tx, int ly, int stage) {
-#define RTK_SM(H, TXV, ST, TT) \
-  if (order == H && tx == TXV && stage == ST) return smem_for<H, TXV, ST, TT>(ly);
+size_t cart_smem_bytes(int order, int storage, int run, int vec, int ly, int stage) {
+#define RTK_SM(O, RR, VV, ST, TT) \
+  if (order == O && run == RR && vec == VV && stage == ST) return cart_smem_for<O, RR, VV, ST, TT>(ly);
   if (storage == 0) { RTK_CART_VARIANTS(RTK_SM, float) } else { RTK_CART_VARIANTS(RTK_SM, __nv_bfloat16) }
 #undef RTK_SM
   return 0;

@@ -91,7 +91,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
   return fn;
 }
 
-static rt_status encode_psi_map(CUtensorMap* map, void* base, int storage, int Mpad, int nx, int ny, int box_x) {
+static rt_status encode_psi_map(CUtensorMap* map, void* base, int storage, int Mpad, int nx, int ny, int box_k,
+                                int box_x) {
   auto enc = get_encode_fn();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -100,7 +101,7 @@ static rt_status encode_psi_map(CUtensorMap* map, void* base, int storage, int M
   const size_t es = storage == RT_BF16 ? 2 : 4;
   cuuint64_t dims[3] = {(cuuint64_t)Mpad, (cuuint64_t)nx, (cuuint64_t)ny};
   cuuint64_t strides[2] = {(cuuint64_t)Mpad * es, (cuuint64_t)nx * Mpad * es};
-  cuuint32_t box[3] = {(cuuint32_t)kChunk, (cuuint32_t)box_x, 1u};
+  cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_x, 1u};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = enc(map, storage == RT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                    base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -249,18 +250,41 @@ static rt_status triangle_metadata(const rt_mesh* m, const int32_t* cell_mat, co
 }
 
 // ---------------------------------------------------------------- tiles
+// Ordinates per lane: the largest V in {4, 2, 1} that divides M_pad/32 and for
+// which every group of V consecutive ordinates has one sign of xi (zero-weight
+// padding ordinates have xi = 0 and fit either sign).
+static int choose_cart_vec(const rt_quadrature* quad, int Mpad) {
+  for (int V = 4; V >= 2; V /= 2) {
+    if ((Mpad / 32) % V != 0) continue;
+    bool ok = true;
+    for (int g0 = 0; g0 < quad->M && ok; g0 += V) {
+      int sgn = 0;
+      for (int k = g0; k < std::min<int64_t>(g0 + V, quad->M); ++k) {
+        const int sk = quad->xi[k] > 0 ? 1 : (quad->xi[k] < 0 ? -1 : 0);
+        if (sk == 0) continue;
+        if (sgn == 0) sgn = sk;
+        else if (sgn != sk) ok = false;
+      }
+    }
+    if (ok) return V;
+  }
+  return 1;
+}
+
 static void choose_cart_tiles(Instance& I, int tile_x, int tile_y) {
-  I.tx = (tile_x == 64) ? 64 : 32;
+  I.run = (tile_x == 32) ? 4 : 2;
+  if (!cart_variant_exists(I.order, I.run, I.cvec)) I.run = 2;
+  I.tx = cart_tile_width(I.run);
   I.n_strips = (I.nx + I.tx - 1) / I.tx;
   const int sms = device_sm_count();
   int ly = tile_y;
   if (ly <= 0) {
-    // smallest grid that still fills every SM a few CTAs deep, with segments long
-    // enough that the 2H halo rows per segment stay a few percent of the reads
-    const int target = 3 * sms;
+    // enough CTAs for a few per SM, with segments long enough that the 2H halo
+    // rows per segment stay a few percent of the rows read
+    const int target = 2 * sms;
     const int segs = std::max(1, (target + I.n_strips - 1) / I.n_strips);
     ly = (I.ny + segs - 1) / segs;
-    ly = std::max(8, std::min(ly, 128));
+    ly = std::max(8, std::min(ly, 64));
   }
   ly = std::max(1, std::min(ly, 256));
   I.ly = ly;
@@ -349,6 +373,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
 
   // --- tiles and work items
   if (I.kind == RT_MESH_CARTESIAN) {
+    I.cvec = choose_cart_vec(quad, I.Mpad);
     choose_cart_tiles(I, tile_x, tile_y);
     I.stage_items.clear();
     const int n = I.n_strips * I.n_segs;
@@ -359,7 +384,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
         I.stage_items.push_back(w);
       }
     const int stage_hi = integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER;
-    I.cart_smem = cart_smem_bytes(order, storage, I.tx, I.ly, stage_hi);
+    I.cart_smem = cart_smem_bytes(order, storage, I.run, I.cvec, I.ly, stage_hi);
     if (I.cart_smem > 227 * 1024) { set_error("tile %dx%d needs %zu bytes of shared memory", I.tx, I.ly, I.cart_smem); return RT_EINVAL; }
   } else {
     cell_range_items(n_cells, I.stage_items);
@@ -436,8 +461,10 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   std::memset(&D, 0, sizeof(D));
   if (I.kind == RT_MESH_CARTESIAN) {
     for (int b = 0; b < 2; ++b)
-      if ((s = encode_psi_map(&D.tm_psi_halo[b], I.psi[b], storage, I.Mpad, I.nx, I.ny, I.tx + 2 * order)) != RT_OK) return s;
-    if ((s = encode_psi_map(&D.tm_psi_center, I.psi[0], storage, I.Mpad, I.nx, I.ny, I.tx)) != RT_OK) return s;
+      if ((s = encode_psi_map(&D.tm_psi_halo[b], I.psi[b], storage, I.Mpad, I.nx, I.ny, 32 * I.cvec,
+                              I.tx + 2 * order)) != RT_OK) return s;
+    if ((s = encode_psi_map(&D.tm_psi_center, I.psi[0], storage, I.Mpad, I.nx, I.ny, 32 * I.cvec, I.tx)) != RT_OK)
+      return s;
   }
   for (int b = 0; b < 2; ++b) { D.psi[b] = I.psi[b]; D.phi[b] = I.phi[b]; }
   D.mat = d_mat; D.region = d_reg;
@@ -446,7 +473,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   D.st = I.st; D.partials = I.partials;
   D.kind = I.kind; D.order = order; D.integrator = integrator; D.storage = storage;
   D.nx = I.nx; D.ny = I.ny; D.M = I.M; D.Mpad = I.Mpad;
-  D.n_chunks = I.Mpad / kChunk; D.tx = I.tx; D.ly = I.ly; D.n_strips = I.n_strips;
+  D.n_chunks = (I.kind == RT_MESH_CARTESIAN) ? I.Mpad / (32 * I.cvec) : I.Mpad / kChunk; D.tx = I.tx; D.ly = I.ly; D.n_strips = I.n_strips;
   D.n_segs = I.n_segs; D.n_items = (int32_t)I.stage_items.size(); D.n_regions = I.n_regions;
   D.n_cells = n_cells; D.n_steps = I.n_steps;
   D.wait_limit = 4000000000LL;   // about two seconds of SM clock
@@ -464,23 +491,37 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     D.sig_s2pi[m] = (float)(ss / (2.0 * M_PI));
     D.q_src[m] = (float)q;
     D.sig_a[m] = sa;
+    D.sig_a_f[m] = (float)sa;
   }
   I.device_bytes = arena.bytes;
   return RT_OK;
 }
 
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
-                      int storage, int order, int tx, int ly_max, int vec, cudaStream_t stream) {
+                      int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream) {
   const int stages[2] = {integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
   const int n_st = integrator == RT_HEUN ? 2 : 1;
   for (int i = 0; i < n_st; ++i) {
     cudaError_t e;
     if (kind == RT_MESH_CARTESIAN)
-      e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, tx, ly_max, stream);
+      e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, run, cvec, ly_max, stream);
     else
       e = launch_tri_stage(d_desc, d_items, n_items, stages[i], storage, vec, stream);
     if (e != cudaSuccess) {
       set_error("stage launch failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  }
+  return RT_OK;
+}
+
+rt_status prepare_instance_kernels(const Instance& I, int ly_max) {
+  if (I.kind != RT_MESH_CARTESIAN) return RT_OK;
+  const int stages[2] = {I.integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
+  for (int i = 0; i < (I.integrator == RT_HEUN ? 2 : 1); ++i) {
+    cudaError_t e = prepare_cart_stage(stages[i], I.order, I.storage, I.run, I.cvec, ly_max);
+    if (e != cudaSuccess) {
+      set_error("kernel set-up failed: %s", cudaGetErrorString(e));
       return RT_ECUDA;
     }
   }

@@ -71,6 +71,7 @@ struct alignas(128) InstDesc {
   float sig_t[kMaxMat];
   float sig_s2pi[kMaxMat];      // sigma_s / (2 pi)
   float q_src[kMaxMat];
+  float sig_a_f[kMaxMat];       // sigma_a as float (per-cell QoI terms; no FP64 in hot loops)
   double sig_a[kMaxMat];
 };
 
@@ -84,10 +85,14 @@ struct WorkItem {
 };
 
 // Launchers (defined in the .cu files). All enqueue on `stream`.
+// Cartesian stage kernel variants: run = cells per thread in x (tile width 8*run),
+// vec = ordinates per lane (chunk of 32*vec ordinates).
 cudaError_t launch_cart_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
-                              int order, int storage, int tx, int ly_max, cudaStream_t stream);
-size_t cart_smem_bytes(int order, int storage, int tx, int ly, int stage);
-cudaError_t prepare_cart_stage(int stage, int order, int storage, int tx, int ly_max);
+                              int order, int storage, int run, int vec, int ly_max, cudaStream_t stream);
+size_t cart_smem_bytes(int order, int storage, int run, int vec, int ly, int stage);
+cudaError_t prepare_cart_stage(int stage, int order, int storage, int run, int vec, int ly_max);
+int cart_tile_width(int run);
+bool cart_variant_exists(int order, int run, int vec);
 cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kTriThreads)
 
   LaneQoI qa;
   qa.init();
-  double bacc = 0.0;
+  float bacc = 0.f;   // FP32 per lane; FP64 from the block reduction on
   int ncell = 0;
   const int c_end = it.a + it.b;
   for (int cell = it.a + warp; cell < c_end; cell += kTriWarps, ++ncell) {
@@ -166,9 +166,9 @@ __global__ void __launch_bounds__(kTriThreads)
     }
     const float ph = warp_sum(phi_part);
     if (lane == 0) phi_out[cell] = ph;
-    if (has_bnd) bacc += (double)bpart * (double)area;
+    bacc += bpart * area;
     if (lane == (ncell & 31)) {
-      qa.keep_va = (float)d.sig_a[m] * area * ph;
+      qa.keep_va = d.sig_a_f[m] * area * ph;
       qa.keep_vm = area * ph;
       qa.keep_reg = reg;
     }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kTriThreads)
     if (g == nreg) acc[g] = (double)qa.fm;
 #pragma unroll
   for (int g = 0; g < kMaxReg + 2; ++g)
-    if (g == nreg + 1) acc[g] = bacc;
+    if (g == nreg + 1) acc[g] = (double)bacc;
   block_reduce_q<kTriThreads>(acc, nreg + 2, red);
   finalize_item<kTriThreads>(d, it, red, STAGE, red + NQ);
 }
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kTriThreads)
 
   LaneQoI qa;
   qa.init();
-  double bacc = 0.0;
+  float bacc = 0.f;
   int ncell = 0;
   for (int cell = it.a + warp; cell < it.a + it.b; cell += kTriWarps, ++ncell) {
     // boundary faces of this cell: (n*l) per face and the side's inflow value
@@ -287,9 +287,9 @@ __global__ void __launch_bounds__(kTriThreads)
     }
     const float ph = warp_sum(ph_part);
     if (lane == 0) phi[cell] = ph;
-    if (nf > 0) bacc += (double)bpart;
+    bacc += bpart;
     if (lane == (ncell & 31)) {
-      qa.keep_va = (float)d.sig_a[m] * area * ph;
+      qa.keep_va = d.sig_a_f[m] * area * ph;
       qa.keep_vm = area * ph;
       qa.keep_reg = reg;
     }
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kTriThreads)
     if (g == nreg) acc[g] = (double)qa.fm;
 #pragma unroll
   for (int g = 0; g < kMaxReg + 2; ++g)
-    if (g == nreg + 1) acc[g] = bacc;
+    if (g == nreg + 1) acc[g] = (double)bacc;
   block_reduce_q<kTriThreads>(acc, nreg + 2, red);
   finalize_item<kTriThreads>(d, it, red, STAGE_INIT, red + NQ);
 }
