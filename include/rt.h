@@ -277,6 +277,71 @@ rt_status rt_batch_get_psi(rt_batch* b, int32_t i, double* host, int64_t n);
 
 void rt_batch_destroy(rt_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * One Cartesian stage without device allocation.
+ *
+ * The paper has no counterpart of this call. Some callers cannot let a library
+ * allocate GPU memory: applications whose device memory is fully reserved by
+ * their own allocator or memory pool (a library cudaMalloc would fail there, or
+ * bypass their accounting), and loops that must not take the implicit device
+ * synchronisation of cudaMalloc/cudaFree. rt_cart_stage_noalloc runs the same
+ * Cartesian stage kernel as rt_step on buffers the caller owns, and allocates
+ * nothing: the kernel's scratch memory (descriptor with TMA tensor maps, work
+ * list, launch state and FP64 partial sums) lives in a fixed file-scope device
+ * array of about 1.4 MB, which every GPU that loads the library keeps until the
+ * process exits. Consequences:
+ *   - grids needing more than RT_NOALLOC_MAX_WORK_ITEMS work items (strips of
+ *     16 cells x tile_y rows) are rejected with RT_EINVAL;
+ *   - every call shares the array; each call clears the parts that must start
+ *     at zero, but calls that overlap on the GPU (e.g. on two streams) race;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ * Arguments (all device pointers unless stated; layout as rt_device_state):
+ *   nx, ny, dx, dy: Cartesian grid; M_pad: ordinates per cell in the psi layout
+ *   [cell][M_pad] (a multiple of 32; padding ordinates must have xi = eta = w = 0);
+ *   vec: ordinates per lane (1, 2 or 4; 0 means 1) - every group of vec
+ *   consecutive ordinates must share the sign of xi; order 1 or 2; stage
+ *   RT_STAGE_EULER / RT_STAGE_HEUN1 (psi_out = psi_in + dt F(psi_in)) or
+ *   RT_STAGE_HEUN2 (psi_out = (psi_n + psi_in + dt F(psi_in))/2; psi_out may be
+ *   psi_n); storage RT_FP32 or RT_BF16; tile_y rows per work item (0 = default);
+ *   material table on the host (n_mat <= 16, n_regions <= 16); inflow psi^- per
+ *   side (x-, x+, y-, y+; 0 = vacuum); dt; psi_in, psi_n, psi_out (16-byte
+ *   aligned, psi_out distinct from psi_in); phi_in = sum_k w_k psi_in,k and
+ *   phi_out (float [cell]); cell_mat, cell_region (uint8 [cell]); xi, eta, w
+ *   (float [M_pad]); qoi_out (double [n_regions + 2]: absorption per region,
+ *   mass, boundary outflow of the output state); status_out (int32, optional:
+ *   0, RT_ETIMEOUT or RT_ENONFINITE once the stream reaches it); stream.
+ * Enqueues on `stream` and returns; RT_EINVAL on invalid arguments (nothing is
+ * launched), RT_ECUDA if a launch fails. */
+#define RT_NOALLOC_MAX_WORK_ITEMS 8192
+enum { RT_STAGE_EULER = 0, RT_STAGE_HEUN1 = 1, RT_STAGE_HEUN2 = 2 };
+typedef struct {
+  int32_t nx, ny;
+  double dx, dy;
+  int32_t M_pad, vec;
+  int32_t order, stage, storage, tile_y;
+  int32_t n_mat, n_regions;
+  double sigma_a[RT_MAX_MATERIALS], sigma_s[RT_MAX_MATERIALS], Q[RT_MAX_MATERIALS];
+  double inflow[4];
+  double dt;
+  const void* psi_in;
+  const void* psi_n;
+  void* psi_out;
+  const float* phi_in;
+  float* phi_out;
+  const uint8_t* cell_mat;
+  const uint8_t* cell_region;
+  const float* xi;
+  const float* eta;
+  const float* w;
+  double* qoi_out;
+  int32_t* status_out;
+  void* stream;
+} rt_cart_stage_args;
+
+rt_status rt_cart_stage_noalloc(const rt_cart_stage_args* args);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,22 @@ class rt_problem(C.Structure):
                 ("order", C.c_int32), ("integrator", C.c_int32), ("dt", C.c_double), ("t_end", C.c_double)]
 
 
+RT_STAGE_EULER, RT_STAGE_HEUN1, RT_STAGE_HEUN2 = 0, 1, 2
+RT_NOALLOC_MAX_WORK_ITEMS = 8192
+
+
+class rt_cart_stage_args(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double), ("dy", C.c_double),
+                ("M_pad", C.c_int32), ("vec", C.c_int32), ("order", C.c_int32), ("stage", C.c_int32),
+                ("storage", C.c_int32), ("tile_y", C.c_int32), ("n_mat", C.c_int32), ("n_regions", C.c_int32),
+                ("sigma_a", C.c_double * 16), ("sigma_s", C.c_double * 16), ("Q", C.c_double * 16),
+                ("inflow", C.c_double * 4), ("dt", C.c_double),
+                ("psi_in", C.c_void_p), ("psi_n", C.c_void_p), ("psi_out", C.c_void_p),
+                ("phi_in", C.c_void_p), ("phi_out", C.c_void_p), ("cell_mat", C.c_void_p),
+                ("cell_region", C.c_void_p), ("xi", C.c_void_p), ("eta", C.c_void_p), ("w", C.c_void_p),
+                ("qoi_out", C.c_void_p), ("status_out", C.c_void_p), ("stream", C.c_void_p)]
+
+
 # exported functions: name -> (restype, argtypes)
 SIGNATURES = {
     "rt_quad_product": (C.c_int, [C.c_int32, C.c_int32, _dp, _dp, _dp, _dp]),
@@ -106,6 +122,7 @@ SIGNATURES = {
     "rt_batch_qoi": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(rt_qoi_t)]),
     "rt_batch_get_psi": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64]),
     "rt_batch_destroy": (None, [C.c_void_p]),
+    "rt_cart_stage_noalloc": (C.c_int, [C.POINTER(rt_cart_stage_args)]),
 }
 
 _lib = None
@@ -217,6 +234,10 @@ def rt_debug_set(h, key: str, value: int):
 def rt_destroy(h):
     if h:
         _fns().rt_destroy(h)
+
+
+def rt_cart_stage_noalloc(args: rt_cart_stage_args):
+    return check(_fns().rt_cart_stage_noalloc(C.byref(args)))
 
 
 def rt_last_error() -> str:
