@@ -119,8 +119,12 @@ typedef void (*rt_free_fn)(void* ptr, void* ctx);
  *     arithmetic is FP32 either way, QoI accumulation FP64).
  *   dt > 0: target step; N_t = ceil(t_end/dt - 1e-9) and dt = t_end/N_t.
  *   dt <= 0: Cartesian 0.5*min(dx,dy); triangles 0.9*min_i 2 A_i / P_i.
- *   tile_x, tile_y: Cartesian tile: cells per strip in x (16 or 32, i.e. runs of 2
- *     or 4 cells per thread) and rows per segment; 0 = chosen by the library.
+ *   tile_x, tile_y: Cartesian tile: cells per strip in x (16; runs of 2 cells per
+ *     thread) and rows per segment (at most 256); 0 = chosen by the library.
+ *   variant: Cartesian kernel variant. 0 = chosen by the library; 1 = per-lane
+ *     flow directions (any quadrature); 2 = chunk-uniform directions, usable when
+ *     every chunk of ordinates has one sign of xi and one of eta (the product
+ *     quadrature's quadrants are contiguous); RT_EINVAL if it is not.
  *   alloc/free/alloc_ctx: device allocator (NULL = cudaMalloc/cudaFree).
  *   stream: cudaStream_t for every launch and copy. */
 typedef struct {
@@ -129,7 +133,7 @@ typedef struct {
   int32_t storage;
   int32_t tile_x;
   int32_t tile_y;
-  int32_t reserved;
+  int32_t variant;
   double dt;
   double t_end;
   rt_alloc_fn alloc;

@@ -40,7 +40,7 @@ rt_status launch_steps_direct(rt_solver* s, int64_t n, cudaStream_t stream) {
   const Instance& I = s->I;
   for (int64_t i = 0; i < n; ++i) {
     rt_status st = launch_step(s->d_desc, s->d_stage_items, (int)I.stage_items.size(), I.kind, I.integrator,
-                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream);
+                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream, I.uni);
     if (st != RT_OK) return st;
   }
   return RT_OK;
@@ -106,7 +106,8 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
   s->stream = (cudaStream_t)opts->stream;
   std::vector<std::vector<char>> keep;
   rt_status st = build_instance(mesh, mat, quad, bc, opts->order, opts->integrator, opts->storage, opts->dt,
-                                opts->t_end, opts->tile_x, opts->tile_y, s->arena, s->stream, s->I, keep);
+                                opts->t_end, opts->tile_x, opts->tile_y, s->arena, s->stream, s->I, keep,
+                                opts->variant);
   auto bail = [&](rt_status code) {
     cudaStreamSynchronize(s->stream);
     (void)cudaGetLastError();

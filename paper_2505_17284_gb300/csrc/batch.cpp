@@ -22,7 +22,7 @@ namespace {
 constexpr int kBatchGraphSteps = 8;
 
 struct Group {
-  int kind, order, run, cvec, vec, ly_max;
+  int kind, order, run, cvec, vec, uni, ly_max;
   int offset, count;
 };
 }  // namespace
@@ -50,7 +50,7 @@ static rt_status enqueue_phase_steps(rt_batch* b, const std::vector<Group>& grou
   for (int64_t i = 0; i < n; ++i) {
     for (const Group& g : groups) {
       rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, b->integrator, b->storage,
-                                 g.order, g.run, g.cvec, g.ly_max, g.vec, stream);
+                                 g.order, g.run, g.cvec, g.ly_max, g.vec, stream, g.uni);
       if (st != RT_OK) return st;
     }
   }
@@ -89,7 +89,8 @@ rt_status rt_batch_create(int32_t k, const rt_problem* problems, const rt_option
   for (int i = 0; i < k; ++i) {
     const rt_problem& P = problems[i];
     rt_status st = build_instance(&P.mesh, &P.mat, &P.quad, &P.bc, P.order, P.integrator, opts->storage, P.dt,
-                                  P.t_end, opts->tile_x, opts->tile_y, b->arena, b->stream, b->inst[i], keep);
+                                  P.t_end, opts->tile_x, opts->tile_y, b->arena, b->stream, b->inst[i], keep,
+                                  opts->variant);
     if (st != RT_OK) {
       char msg[1200];
       snprintf(msg, sizeof(msg), "problem %d: %s", i, rt_last_error());
@@ -166,17 +167,17 @@ rt_status rt_batch_run(rt_batch* b, int64_t max_steps) {
       if (b->done[i] < target[i]) phase = std::min(phase, target[i] - b->done[i]);
     if (phase == INT64_MAX) break;
     // work list of the unfinished problems, grouped by kernel variant
-    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> by_variant;
+    std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> by_variant;
     for (int i = 0; i < k; ++i) {
       if (b->done[i] >= target[i]) continue;
       const Instance& I = b->inst[i];
-      by_variant[std::make_tuple(I.kind, I.order, I.run, I.cvec, I.vec)].push_back(i);
+      by_variant[std::make_tuple(I.kind, I.order, I.run, I.cvec, I.vec, I.uni)].push_back(i);
     }
     std::vector<WorkItem> items;
     std::vector<Group> groups;
     for (auto& kv : by_variant) {
       Group g{};
-      std::tie(g.kind, g.order, g.run, g.cvec, g.vec) = kv.first;
+      std::tie(g.kind, g.order, g.run, g.cvec, g.vec, g.uni) = kv.first;
       g.offset = (int)items.size();
       g.ly_max = 1;
       for (int i : kv.second) {

@@ -271,9 +271,34 @@ static int choose_cart_vec(const rt_quadrature* quad, int Mpad) {
   return 1;
 }
 
+// Chunk-uniform check: for chunks of 32V ordinates, every chunk has one sign of
+// xi and one of eta (zeros fit either). Fills the per-chunk directions.
+static bool chunks_uniform(const rt_quadrature* quad, int Mpad, int V, int8_t* dx, int8_t* dy) {
+  const int C = 32 * V;
+  if (Mpad % C != 0 || Mpad / C > kMaxUniChunks) return false;
+  for (int c = 0; c < Mpad / C; ++c) {
+    int sx = 0, sy = 0;
+    for (int k = c * C; k < std::min<int64_t>((int64_t)(c + 1) * C, quad->M); ++k) {
+      const int kx = quad->xi[k] > 0 ? 1 : (quad->xi[k] < 0 ? -1 : 0);
+      const int ky = quad->eta[k] > 0 ? 1 : (quad->eta[k] < 0 ? -1 : 0);
+      if (kx != 0) {
+        if (sx == 0) sx = kx;
+        else if (sx != kx) return false;
+      }
+      if (ky != 0) {
+        if (sy == 0) sy = ky;
+        else if (sy != ky) return false;
+      }
+    }
+    dx[c] = (int8_t)(sx < 0 ? -1 : 1);
+    dy[c] = (int8_t)(sy < 0 ? -1 : 1);
+  }
+  return true;
+}
+
 static void choose_cart_tiles(Instance& I, int tile_x, int tile_y) {
-  I.run = (tile_x == 32) ? 4 : 2;
-  if (!cart_variant_exists(I.order, I.run, I.cvec)) I.run = 2;
+  (void)tile_x;   // one tile width (16 cells) in this build
+  I.run = 2;
   I.tx = cart_tile_width(I.run);
   I.n_strips = (I.nx + I.tx - 1) / I.tx;
   const int sms = device_sm_count();
@@ -313,7 +338,7 @@ static void cell_range_items(int64_t n_cells, std::vector<WorkItem>& items) {
 rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
                          const rt_boundary* bc, int order, int integrator, int storage, double dt_target,
                          double t_end, int tile_x, int tile_y, DeviceArena& arena, cudaStream_t stream,
-                         Instance& I, std::vector<std::vector<char>>& keep) {
+                         Instance& I, std::vector<std::vector<char>>& keep, int variant) {
   if (!mesh) { set_error("mesh is NULL"); return RT_EINVAL; }
   int64_t n_cells = 0;
   if (mesh->kind == RT_MESH_CARTESIAN) {
@@ -372,8 +397,27 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   I.source_rate = aq * wsum;
 
   // --- tiles and work items
+  int8_t cdx[kMaxUniChunks] = {0}, cdy[kMaxUniChunks] = {0};
   if (I.kind == RT_MESH_CARTESIAN) {
+    if (variant < 0 || variant > 2) { set_error("variant must be 0, 1 or 2"); return RT_EINVAL; }
+    // per-lane width first; the chunk-uniform variant is taken (automatically) when
+    // the same width also gives sign-uniform chunks, or when asked for
+    I.uni = 0;
     I.cvec = choose_cart_vec(quad, I.Mpad);
+    if (variant != 1) {
+      for (int V = (variant == 2 ? 4 : I.cvec); V >= 2; V /= 2) {
+        if (chunks_uniform(quad, I.Mpad, V, cdx, cdy)) {
+          I.uni = 1;
+          I.cvec = V;
+          break;
+        }
+        if (variant == 0) break;
+      }
+      if (variant == 2 && !I.uni) {
+        set_error("variant 2 needs every ordinate chunk to have one sign of xi and one of eta");
+        return RT_EINVAL;
+      }
+    }
     choose_cart_tiles(I, tile_x, tile_y);
     I.stage_items.clear();
     const int n = I.n_strips * I.n_segs;
@@ -387,7 +431,15 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     I.cart_smem = cart_smem_bytes(order, storage, I.run, I.cvec, I.ly, stage_hi);
     if (I.cart_smem > 227 * 1024) { set_error("tile %dx%d needs %zu bytes of shared memory", I.tx, I.ly, I.cart_smem); return RT_EINVAL; }
   } else {
-    cell_range_items(n_cells, I.stage_items);
+    // persistent work items: item g processes 64-cell chunks g, g + G, ...
+    const int64_t n_chunks = (n_cells + 63) / 64;
+    const int G = (int)std::min<int64_t>(n_chunks, 3LL * device_sm_count());
+    I.stage_items.clear();
+    for (int g = 0; g < G; ++g) {
+      WorkItem w{};
+      w.inst = 0; w.a = g; w.b = G; w.item = g; w.count = G;
+      I.stage_items.push_back(w);
+    }
   }
   cell_range_items(n_cells, I.init_items);
 
@@ -484,6 +536,11 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   }
   D.dt = (float)I.dt; D.dt_d = I.dt;
   for (int sd = 0; sd < 4; ++sd) D.ghost[sd] = bc->side_kind[sd] == RT_BC_INFLOW ? (float)bc->inflow[sd] : 0.f;
+  D.uni = I.uni;
+  for (int c = 0; c < kMaxUniChunks; ++c) {
+    D.cdir_x[c] = cdx[c];
+    D.cdir_y[c] = cdy[c];
+  }
   for (int m = 0; m < kMaxMat; ++m) {
     const bool in = m < mat->n_mat;
     const double sa = in ? mat->sigma_a[m] : 0.0, ss = in ? mat->sigma_s[m] : 0.0, q = in ? mat->Q[m] : 0.0;
@@ -498,13 +555,14 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
 }
 
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
-                      int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream) {
+                      int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream,
+                      int uni) {
   const int stages[2] = {integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
   const int n_st = integrator == RT_HEUN ? 2 : 1;
   for (int i = 0; i < n_st; ++i) {
     cudaError_t e;
     if (kind == RT_MESH_CARTESIAN)
-      e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, run, cvec, ly_max, stream);
+      e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, run, cvec, ly_max, stream, uni);
     else
       e = launch_tri_stage(d_desc, d_items, n_items, stages[i], storage, vec, stream);
     if (e != cudaSuccess) {
@@ -519,7 +577,7 @@ rt_status prepare_instance_kernels(const Instance& I, int ly_max) {
   if (I.kind != RT_MESH_CARTESIAN) return RT_OK;
   const int stages[2] = {I.integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
   for (int i = 0; i < (I.integrator == RT_HEUN ? 2 : 1); ++i) {
-    cudaError_t e = prepare_cart_stage(stages[i], I.order, I.storage, I.run, I.cvec, ly_max);
+    cudaError_t e = prepare_cart_stage(stages[i], I.order, I.storage, I.run, I.cvec, ly_max, I.uni);
     if (e != cudaSuccess) {
       set_error("kernel set-up failed: %s", cudaGetErrorString(e));
       return RT_ECUDA;

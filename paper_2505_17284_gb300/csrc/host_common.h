@@ -48,6 +48,7 @@ struct Instance {
   int64_t n_steps = 0;
   int32_t tx = 16, ly = 32, n_strips = 0, n_segs = 0;
   int32_t run = 2, cvec = 1;        // Cartesian kernel: cells per thread, ordinates per lane
+  int32_t uni = 0;                  // Cartesian kernel: chunk-uniform flow directions
   int32_t n_regions = 0;
   double source_rate = 0;   // 2 pi sum_i A_i Q_i
   size_t cart_smem = 0;
@@ -68,14 +69,15 @@ struct Instance {
 rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
                          const rt_boundary* bc, int order, int integrator, int storage, double dt, double t_end,
                          int tile_x, int tile_y, DeviceArena& arena, cudaStream_t stream, Instance& inst,
-                         std::vector<std::vector<char>>& host_keepalive);
+                         std::vector<std::vector<char>>& host_keepalive, int variant = 0);
 
 int device_sm_count();
 
 // Launch the stage(s) of one time step for the given instances' work items.
 // `run`/`cvec` select the Cartesian variant, `vec` the triangle vector width.
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
-                      int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream);
+                      int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream,
+                      int uni = 0);
 rt_status prepare_instance_kernels(const Instance& I, int ly_max);
 
 // Synchronise `stream` and read an instance's device state; maps device status

@@ -21,6 +21,7 @@ constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
 constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
 constexpr int kChunk = 32;             // ordinates per chunk (one per lane)
+constexpr int kMaxUniChunks = 64;      // chunk-uniform variant: at most this many ordinate chunks
 
 enum Stage : int32_t { STAGE_EULER = 0, STAGE_HEUN1 = 1, STAGE_HEUN2 = 2, STAGE_INIT = 3 };
 enum Kind : int32_t { KIND_CART = 0, KIND_TRI = 1 };
@@ -68,6 +69,9 @@ struct alignas(128) InstDesc {
   float inv_dx, inv_dy, dt, pad2;
   double dt_d, area_d, dx_d, dy_d;  // Cartesian cell area and sizes (FP64 QoIs)
   float ghost[4];               // inflow value per side (entering ordinates)
+  int32_t uni;                  // 1: every ordinate chunk has one sign of xi and one of eta
+  int8_t cdir_x[kMaxUniChunks]; // per chunk: sign of xi (+1/-1) when uni
+  int8_t cdir_y[kMaxUniChunks]; // per chunk: sign of eta
   float sig_t[kMaxMat];
   float sig_s2pi[kMaxMat];      // sigma_s / (2 pi)
   float q_src[kMaxMat];
@@ -87,12 +91,14 @@ struct WorkItem {
 // Launchers (defined in the .cu files). All enqueue on `stream`.
 // Cartesian stage kernel variants: run = cells per thread in x (tile width 8*run),
 // vec = ordinates per lane (chunk of 32*vec ordinates).
+// uni = 1 selects the chunk-uniform variant (InstDesc::cdir_x/y set per chunk).
 cudaError_t launch_cart_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
-                              int order, int storage, int run, int vec, int ly_max, cudaStream_t stream);
+                              int order, int storage, int run, int vec, int ly_max, cudaStream_t stream,
+                              int uni = 0);
 size_t cart_smem_bytes(int order, int storage, int run, int vec, int ly, int stage);
-cudaError_t prepare_cart_stage(int stage, int order, int storage, int run, int vec, int ly_max);
+cudaError_t prepare_cart_stage(int stage, int order, int storage, int run, int vec, int ly_max, int uni = 0);
 int cart_tile_width(int run);
-bool cart_variant_exists(int order, int run, int vec);
+bool cart_variant_exists(int order, int run, int vec, int uni = 0);
 cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,

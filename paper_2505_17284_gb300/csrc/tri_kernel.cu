@@ -71,10 +71,21 @@ struct LaneQoI {
   }
 };
 
+// Persistent stage kernel: work item g of G processes the 64-cell chunks
+// g, g + G, g + 2G, ... in increasing order, so all SMs sweep the mesh together
+// and the rows of the neighbouring grid row (2n cells away on the split grid)
+// are still in L2 when they are gathered. Warp w takes cells w, w + 8, ... of a
+// chunk, so neighbours one cell apart are fetched by adjacent warps at the same
+// time (L1). QoI terms are summed per warp in shared memory (FP32 over 32
+// cells, then FP64).
+constexpr int kTriChunk = 64;
+
 template <int VEC, int STAGE, typename T>
-__global__ void __launch_bounds__(kTriThreads)
+__global__ void __launch_bounds__(kTriThreads, 3)
     tri_stage_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
   __shared__ double red[(kTriWarps + 1) * NQ];
+  __shared__ float wacc[kTriWarps][NQ];
+  __shared__ double wdacc[kTriWarps][NQ];
   const WorkItem it = items[blockIdx.x];
   const InstDesc& d = descs[it.inst];
   InstState* st = d.st;
@@ -92,104 +103,112 @@ __global__ void __launch_bounds__(kTriThreads)
   const int Mpad = d.Mpad;
   const int nv = Mpad / (32 * VEC);
   const float dt = d.dt;
+  const int nreg = d.n_regions, nq = nreg + 2;
+  const int n_cells = (int)d.n_cells;
+  const int n_chunks = (n_cells + kTriChunk - 1) / kTriChunk;
 
-  LaneQoI qa;
-  qa.init();
-  float bacc = 0.f;   // FP32 per lane; FP64 from the block reduction on
+  if (lane < NQ) {
+    wacc[warp][lane] = 0.f;
+    wdacc[warp][lane] = 0.0;
+  }
+  __syncwarp();
   int ncell = 0;
-  const int c_end = it.a + it.b;
-  for (int cell = it.a + warp; cell < c_end; cell += kTriWarps, ++ncell) {
-    const int4 nb = __ldg(&d.tri_nbr[cell]);
-    const float4 g0 = __ldg(&d.tri_geo[2 * (size_t)cell]);
-    const float4 g1 = __ldg(&d.tri_geo[2 * (size_t)cell + 1]);
-    const float ax[3] = {g0.x, g0.z, g1.x};
-    const float ay[3] = {g0.y, g0.w, g1.y};
-    const int nbr[3] = {nb.x, nb.y, nb.z};
-    const int m = nb.w & 255, reg = (nb.w >> 8) & 255;
-    const float area = g1.z;
-    const float sig_t = d.sig_t[m];
-    const float src = d.sig_s2pi[m] * phi_in[cell] + d.q_src[m];
-    const bool has_bnd = (nbr[0] < 0) | (nbr[1] < 0) | (nbr[2] < 0);
-    float gh[3];
+  for (int k = it.a; k < n_chunks; k += it.b) {
+    const int c_end = min(n_cells, (k + 1) * kTriChunk);
+    for (int cell = k * kTriChunk + warp; cell < c_end; cell += kTriWarps) {
+      const int4 nb = __ldg(&d.tri_nbr[cell]);
+      const float4 g0 = __ldg(&d.tri_geo[2 * (size_t)cell]);
+      const float4 g1 = __ldg(&d.tri_geo[2 * (size_t)cell + 1]);
+      const float ax[3] = {g0.x, g0.z, g1.x};
+      const float ay[3] = {g0.y, g0.w, g1.y};
+      const int nbr[3] = {nb.x, nb.y, nb.z};
+      const int m = nb.w & 255, reg = (nb.w >> 8) & 255;
+      const float area = g1.z;
+      const float sig_t = d.sig_t[m];
+      const float src = d.sig_s2pi[m] * phi_in[cell] + d.q_src[m];
+      const bool has_bnd = (nbr[0] < 0) | (nbr[1] < 0) | (nbr[2] < 0);
+      float gh[3];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) gh[e] = (nbr[e] < 0) ? d.ghost[-1 - nbr[e]] : 0.f;
+      for (int e = 0; e < 3; ++e) gh[e] = (nbr[e] < 0) ? d.ghost[-1 - nbr[e]] : 0.f;
 
-    float phi_part = 0.f, bpart = 0.f;
-    for (int v = 0; v < nv; ++v) {
-      const int k = (v * 32 + lane) * VEC;
-      float c[VEC], nbv[3][VEC], xi[VEC], eta[VEC], w[VEC];
-      load_vec<T, VEC>(psi_in + (size_t)cell * Mpad + k, c);
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        if (nbr[e] >= 0) {
-          load_vec<T, VEC>(psi_in + (size_t)nbr[e] * Mpad + k, nbv[e]);
-        } else {
-#pragma unroll
-          for (int l = 0; l < VEC; ++l) nbv[e][l] = gh[e];
-        }
-      }
-      load_vec<float, VEC>(d.xi + k, xi);
-      load_vec<float, VEC>(d.eta + k, eta);
-      load_vec<float, VEC>(d.w + k, w);
-      float base[VEC];
-      if constexpr (STAGE == STAGE_HEUN2) load_vec<T, VEC>(psi_base + (size_t)cell * Mpad + k, base);
-      float out[VEC];
-#pragma unroll
-      for (int l = 0; l < VEC; ++l) {
-        float div = 0.f;
+      float phi_part = 0.f, bpart = 0.f;
+      for (int v = 0; v < nv; ++v) {
+        const int kk = (v * 32 + lane) * VEC;
+        float c[VEC], nbv[3][VEC], xi[VEC], eta[VEC], w[VEC];
+        load_vec<T, VEC>(psi_in + (size_t)cell * Mpad + kk, c);
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-          const float on = xi[l] * ax[e] + eta[l] * ay[e];
-          div += on * ((on > 0.f) ? c[l] : nbv[e][l]);
+          if (nbr[e] >= 0) {
+            load_vec<T, VEC>(psi_in + (size_t)nbr[e] * Mpad + kk, nbv[e]);
+          } else {
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) nbv[e][l] = gh[e];
+          }
         }
-        const float F = -div - sig_t * c[l] + src;
-        float o;
-        if constexpr (STAGE == STAGE_HEUN2) {
-          o = 0.5f * (base[l] + c[l] + dt * F);
-        } else {
-          o = c[l] + dt * F;
-        }
-        o = Store<T>::round(o);
-        out[l] = o;
-        phi_part += w[l] * o;
-        if (has_bnd) {
+        load_vec<float, VEC>(d.xi + kk, xi);
+        load_vec<float, VEC>(d.eta + kk, eta);
+        load_vec<float, VEC>(d.w + kk, w);
+        float base[VEC];
+        if constexpr (STAGE == STAGE_HEUN2) load_vec<T, VEC>(psi_base + (size_t)cell * Mpad + kk, base);
+        float out[VEC];
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+          float div = 0.f;
 #pragma unroll
           for (int e = 0; e < 3; ++e) {
-            if (nbr[e] < 0) {
-              const float on = xi[l] * ax[e] + eta[l] * ay[e];
-              bpart += w[l] * on * ((on > 0.f) ? o : gh[e]);
+            const float on = xi[l] * ax[e] + eta[l] * ay[e];
+            div += on * ((on > 0.f) ? c[l] : nbv[e][l]);
+          }
+          const float F = -div - sig_t * c[l] + src;
+          float o;
+          if constexpr (STAGE == STAGE_HEUN2) {
+            o = 0.5f * (base[l] + c[l] + dt * F);
+          } else {
+            o = c[l] + dt * F;
+          }
+          o = Store<T>::round(o);
+          out[l] = o;
+          phi_part += w[l] * o;
+          if (has_bnd) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+              if (nbr[e] < 0) {
+                const float on = xi[l] * ax[e] + eta[l] * ay[e];
+                bpart += w[l] * on * ((on > 0.f) ? o : gh[e]);
+              }
             }
           }
         }
+        store_vec<T, VEC>(psi_out + (size_t)cell * Mpad + kk, out);
       }
-      store_vec<T, VEC>(psi_out + (size_t)cell * Mpad + k, out);
+      const float ph = warp_sum(phi_part);
+      float bsum = 0.f;
+      if (has_bnd) bsum = warp_sum(bpart);
+      if (lane == 0) {
+        phi_out[cell] = ph;
+        wacc[warp][reg] += d.sig_a_f[m] * area * ph;
+        wacc[warp][nreg] += area * ph;
+        wacc[warp][nreg + 1] += bsum * area;
+      }
+      if ((++ncell & 31) == 0) {
+        __syncwarp();
+        if (lane < nq) {
+          wdacc[warp][lane] += (double)wacc[warp][lane];
+          wacc[warp][lane] = 0.f;
+        }
+        __syncwarp();
+      }
     }
-    const float ph = warp_sum(phi_part);
-    if (lane == 0) phi_out[cell] = ph;
-    bacc += bpart * area;
-    if (lane == (ncell & 31)) {
-      qa.keep_va = d.sig_a_f[m] * area * ph;
-      qa.keep_vm = area * ph;
-      qa.keep_reg = reg;
-    }
-    if ((ncell & 31) == 31) qa.flush();
   }
-  qa.flush();
-
-  const int nreg = d.n_regions;
-  double acc[NQ];
-#pragma unroll
-  for (int g = 0; g < NQ; ++g) acc[g] = 0.0;
-#pragma unroll
-  for (int g = 0; g < kMaxReg; ++g)
-    if (g < nreg) acc[g] = (double)qa.fa[g];
-#pragma unroll
-  for (int g = 0; g < kMaxReg + 1; ++g)
-    if (g == nreg) acc[g] = (double)qa.fm;
-#pragma unroll
-  for (int g = 0; g < kMaxReg + 2; ++g)
-    if (g == nreg + 1) acc[g] = (double)bacc;
-  block_reduce_q<kTriThreads>(acc, nreg + 2, red);
+  __syncwarp();
+  if (lane < nq) wdacc[warp][lane] += (double)wacc[warp][lane];
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < kTriWarps; ++w2) s += wdacc[w2][threadIdx.x];
+    red[threadIdx.x] = s;
+  }
+  __syncthreads();
   finalize_item<kTriThreads>(d, it, red, STAGE, red + NQ);
 }
 

@@ -57,7 +57,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class rt_options(C.Structure):
     _fields_ = [("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
-                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("reserved", C.c_int32),
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("variant", C.c_int32),
                 ("dt", C.c_double), ("t_end", C.c_double),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p)]
 
@@ -328,10 +328,10 @@ class TorchAllocator:
 
 
 def make_options(order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=1.0, tile_x=0, tile_y=0,
-                 allocator: TorchAllocator | None = None, stream=None) -> rt_options:
+                 allocator: TorchAllocator | None = None, stream=None, variant=0) -> rt_options:
     o = rt_options()
     o.order, o.integrator, o.storage = order, integrator, storage
-    o.tile_x, o.tile_y = tile_x, tile_y
+    o.tile_x, o.tile_y, o.variant = tile_x, tile_y, variant
     o.dt, o.t_end = dt, t_end
     if allocator is not None:
         allocator.fill(o)
@@ -344,12 +344,12 @@ class Solver:
     """One problem on the GPU: create -> step -> qoi, through the C ABI."""
 
     def __init__(self, problem, quad, order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=None,
-                 tile_x=0, tile_y=0, use_torch_allocator=True):
+                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0):
         keep = _Keep()
         mesh, mat, q, bc = make_structs(problem, quad, keep)
         self.allocator = TorchAllocator() if use_torch_allocator else None
         opts = make_options(order, integrator, storage, dt, problem.t_end if t_end is None else t_end,
-                            tile_x, tile_y, self.allocator)
+                            tile_x, tile_y, self.allocator, variant=variant)
         self.h = rt_create(mesh, mat, q, bc, opts)
         self.info = rt_info(self.h)
         self.n_cells, self.M = int(self.info.n_cells), int(self.info.M)
@@ -391,7 +391,7 @@ class Batch:
     """Many problems advanced together (rt_batch_*)."""
 
     def __init__(self, problems, quads, order=2, integrator=RT_HEUN, storage=RT_FP32, dts=None,
-                 tile_x=0, tile_y=0, use_torch_allocator=True):
+                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0):
         keep = _Keep()
         k = len(problems)
         arr = (rt_problem * k)()
@@ -405,7 +405,7 @@ class Batch:
             arr[i].t_end = p.t_end
             self.shapes.append((p.mesh.n_cells, len(qd[0]), mat.n_regions))
         self.allocator = TorchAllocator() if use_torch_allocator else None
-        opts = make_options(storage=storage, tile_x=tile_x, tile_y=tile_y, allocator=self.allocator)
+        opts = make_options(storage=storage, tile_x=tile_x, tile_y=tile_y, allocator=self.allocator, variant=variant)
         self.h = C.c_void_p()
         check(_fns().rt_batch_create(k, arr, C.byref(opts), C.byref(self.h)))
         self.k = k

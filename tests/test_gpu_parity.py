@@ -115,17 +115,34 @@ def test_random_state_one_step_elementwise(rt, order, integrator):
     check_qoi(q, acc, S, 3, scale=S["mass"])
 
 
-@pytest.mark.parametrize("n_p,n_phi,tile_x,expect_tx", [(4, 16, 32, 32), (4, 16, 16, 16), (8, 16, 0, 16),
-                                                        (2, 16, 32, 32)])
-def test_kernel_variants(rt, n_p, n_phi, tile_x, expect_tx):
-    """Run lengths (tile widths 16 and 32 cells) and ordinates per lane (1, 2, 4)
-    on a 91^2 grid (ragged for both widths) from a smooth state."""
+@pytest.mark.parametrize("n_p,n_phi,variant", [(4, 16, 0), (8, 16, 0), (2, 16, 0), (8, 32, 1), (8, 32, 2),
+                                               (16, 32, 1), (16, 32, 2), (4, 64, 2)])
+@pytest.mark.parametrize("order", [1, 2])
+def test_kernel_variants(rt, n_p, n_phi, variant, order):
+    """Ordinates per lane (1, 2, 4) and both direction families (per-lane and
+    chunk-uniform) on a 91^2 grid (ragged tiles) from a smooth state, Heun."""
     p = si.lattice_problem(91)
     psi0 = si.smooth_psi(p.mesh, n_p * n_phi, seed=3)
-    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, n_p, n_phi, 2, rt.RT_HEUN, 5, psi0=psi0,
-                                                  dt=0.5 * p.mesh.dx, tile_x=tile_x)
-    assert info.tile_x == expect_tx
+    quad_lib = rt.rt_quad_product(n_p, n_phi)
+    s = rt.Solver(p, quad_lib, order=order, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, variant=variant)
+    s.set_psi(psi0)
+    s.step(5)
+    psi, q, dt = s.psi(), s.qoi(), s.info.dt
+    s.close()
+    op = oracle.CartesianOracle(p, oracle.product_quadrature(n_p, n_phi), order=order)
+    ref, acc, S = oracle.run(op, psi0, dt, 5, "heun")
     assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_uniform_variant_rejected_for_mixed_chunks(rt):
+    p = si.lattice_problem(14)
+    xi = np.array([0.6, -0.6] * 32)
+    eta = np.array([0.5] * 64)
+    quad = (xi, eta, np.sqrt(1 - xi ** 2 - eta ** 2), np.full(64, 2 * math.pi / 64))
+    with pytest.raises(rt.RTError) as e:
+        rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.25, variant=2)
+    assert e.value.code == rt.RT_EINVAL
 
 
 def test_mixed_sign_quadrature_groups(rt):
