@@ -119,12 +119,15 @@ typedef void (*rt_free_fn)(void* ptr, void* ctx);
  *     arithmetic is FP32 either way, QoI accumulation FP64).
  *   dt > 0: target step; N_t = ceil(t_end/dt - 1e-9) and dt = t_end/N_t.
  *   dt <= 0: Cartesian 0.5*min(dx,dy); triangles 0.9*min_i 2 A_i / P_i.
- *   tile_x, tile_y: Cartesian tile: cells per strip in x (16; runs of 2 cells per
- *     thread) and rows per segment (at most 256); 0 = chosen by the library.
+ *   tile_x, tile_y: Cartesian tile: cells per strip in x (16: runs of 2 cells per
+ *     warp; 32: runs of 4, which needs chunk-uniform directions with 2 ordinates
+ *     per lane) and rows per segment (at most 256); 0 = chosen by the library.
  *   variant: Cartesian kernel variant. 0 = chosen by the library; 1 = per-lane
  *     flow directions (any quadrature); 2 = chunk-uniform directions, usable when
  *     every chunk of ordinates has one sign of xi and one of eta (the product
  *     quadrature's quadrants are contiguous); RT_EINVAL if it is not.
+ *   vec: Cartesian ordinates per lane (1, 2 or 4; 0 = chosen by the library);
+ *     RT_EINVAL if the quadrature does not allow it (see rt_info_t for the choice).
  *   alloc/free/alloc_ctx: device allocator (NULL = cudaMalloc/cudaFree).
  *   stream: cudaStream_t for every launch and copy. */
 typedef struct {
@@ -140,6 +143,8 @@ typedef struct {
   rt_free_fn free;
   void* alloc_ctx;
   void* stream;
+  int32_t vec;
+  int32_t pad;
 } rt_options;
 
 /* QoIs (Sec. 3.1 QoI-3..5, Sec. 3.2 QoI-2, QoI-7), FP64:
@@ -245,11 +250,15 @@ const char* rt_last_error(void);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent problems advanced together by shared launches.
- * Each stage is one launch over the work items of every unfinished problem
- * (finished problems are masked on the device), and rt_batch_run replays a
- * CUDA graph of `graph_steps` steps until every problem reaches its own N_t.
- * The paper has no batching; problems are the lattice design-parameter
- * sweeps of Sec. 3.1.3 (DP-1) solved side by side.
+ * The paper has no batching; the problems are, for example, the lattice
+ * design-parameter sweeps of Sec. 3.1.3 (DP-1) or a stream of solve requests.
+ * A batch has a fixed number of slots. Each stage of a step is one launch per
+ * kernel variant over the work items of every unfinished problem (finished
+ * problems are also masked on the device), so many small problems fill the GPU
+ * together. Problems may differ in mesh kind, grid, ordinates, order and
+ * integrator; they share the storage type, allocator and stream. Problems can
+ * be added and removed between steps (continuous batching); each problem's
+ * device memory is its own and is freed when it is removed.
  * ------------------------------------------------------------------------- */
 typedef struct {
   rt_mesh mesh;
@@ -258,26 +267,50 @@ typedef struct {
   rt_boundary bc;
   int32_t order;
   int32_t integrator;
-  double dt;
+  double dt;       /* as rt_options.dt */
   double t_end;
+  int32_t tile_y;  /* as rt_options; 0 = the batch options' value */
+  int32_t variant;
+  int32_t vec;
+  int32_t pad;
 } rt_problem;
 
 typedef struct rt_batch rt_batch;
 
-/* Create a batch of k problems sharing storage type, allocator and stream from
- * opts (opts.order/integrator/dt/t_end are ignored; each problem has its own).
- * All problems must use the same integrator. Errors as rt_create. */
-rt_status rt_batch_create(int32_t k, const rt_problem* problems, const rt_options* opts, rt_batch** out);
+/* Create a batch with `capacity` slots (0 = k) holding the k problems given
+ * (slots 0..k-1, k may be 0). Storage, allocator, stream and default kernel
+ * options come from opts (its order/integrator/dt/t_end are not used).
+ * Errors as rt_create; on failure *out is NULL and nothing is leaked. */
+rt_status rt_batch_create(int32_t k, const rt_problem* problems, int32_t capacity, const rt_options* opts,
+                          rt_batch** out);
 
-/* Advance every problem to its own N_t (at most max_steps steps per problem when
- * max_steps > 0); enqueues graph replays on the stream and returns. */
+/* Add a problem in a free slot; *slot receives its index. Creates and
+ * initialises its device state (synchronises the stream). RT_EINVAL if the
+ * problem is invalid or no slot is free, RT_ENOMEM if the allocator fails;
+ * the batch is unchanged then. */
+rt_status rt_batch_add(rt_batch* b, const rt_problem* problem, int32_t* slot);
+
+/* Remove the problem in `slot` and free its device memory (synchronises). */
+rt_status rt_batch_remove(rt_batch* b, int32_t slot);
+
+/* Enqueue up to n steps of every unfinished problem (each stops at its own
+ * N_t) and return. While the set of unfinished problems and n stay the same,
+ * calls replay one captured CUDA graph. */
+rt_status rt_batch_step(rt_batch* b, int64_t n);
+
+/* Advance every problem to its own N_t (at most max_steps steps per problem
+ * when max_steps > 0); enqueues and returns. */
 rt_status rt_batch_run(rt_batch* b, int64_t max_steps);
 
-/* Synchronise and copy problem i's QoIs. */
-rt_status rt_batch_qoi(rt_batch* b, int32_t i, rt_qoi_t* out);
+/* Steps enqueued so far for the problem in `slot` and its N_t (no
+ * synchronisation). RT_EINVAL for an empty slot. */
+rt_status rt_batch_progress(const rt_batch* b, int32_t slot, int64_t* steps_done, int64_t* n_steps);
 
-/* Copy problem i's psi ([cell][k] doubles, n = n_cells*M). */
-rt_status rt_batch_get_psi(rt_batch* b, int32_t i, double* host, int64_t n);
+/* Synchronise and copy the QoIs of the problem in `slot`. */
+rt_status rt_batch_qoi(rt_batch* b, int32_t slot, rt_qoi_t* out);
+
+/* Copy psi of the problem in `slot` ([cell][k] doubles, n = n_cells*M). */
+rt_status rt_batch_get_psi(rt_batch* b, int32_t slot, double* host, int64_t n);
 
 void rt_batch_destroy(rt_batch* b);
 

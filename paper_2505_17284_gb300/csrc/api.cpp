@@ -107,7 +107,7 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
   std::vector<std::vector<char>> keep;
   rt_status st = build_instance(mesh, mat, quad, bc, opts->order, opts->integrator, opts->storage, opts->dt,
                                 opts->t_end, opts->tile_x, opts->tile_y, s->arena, s->stream, s->I, keep,
-                                opts->variant);
+                                opts->variant, opts->vec);
   auto bail = [&](rt_status code) {
     cudaStreamSynchronize(s->stream);
     (void)cudaGetLastError();

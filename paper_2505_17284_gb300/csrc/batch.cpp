@@ -1,16 +1,19 @@
 // Batches of independent S_N problems advanced by shared launches.
 //
-// All problems' descriptors sit in one device array; a stage launch covers the
-// work items of every unfinished problem of one kernel variant (mesh kind,
-// order, tile width, vector width), so many small problems fill the GPU
-// together instead of one launch each. rt_batch_run proceeds in phases: a phase
-// lasts until the next problem reaches its own N_t, its work list holds only
-// unfinished problems, and its steps replay a captured CUDA graph of
-// kBatchGraphSteps steps (plus direct launches for the remainder). The kernels
-// also mask finished problems on the device.
+// A batch has `capacity` slots. The descriptors of all slots sit in one device
+// array; a stage launch covers the work items of every unfinished problem of
+// one kernel variant (mesh kind, order, integrator and the Cartesian or
+// triangle variant knobs), so many small problems fill the GPU together
+// instead of one launch each. Problems can be added and removed between steps;
+// each slot owns its device memory (its own allocation list), freed on removal.
+// rt_batch_step enqueues up to n steps for the unfinished problems; while the
+// membership and n stay the same it replays one captured CUDA graph. Problems
+// past their own N_t are dropped from the work list at the next step and are
+// also masked on the device.
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <tuple>
 #include <vector>
 
@@ -19,252 +22,385 @@
 using namespace rtk;
 
 namespace {
-constexpr int kBatchGraphSteps = 8;
 
 struct Group {
-  int kind, order, run, cvec, vec, uni, ly_max;
+  int kind, order, integrator, run, cvec, vec, uni, ly_max;
   int offset, count;
 };
+
+struct Slot {
+  bool used = false;
+  std::unique_ptr<DeviceArena> arena;
+  Instance inst;
+  WorkItem* d_init_items = nullptr;
+  int64_t done = 0;   // steps enqueued
+};
+
 }  // namespace
 
 struct rt_batch {
-  DeviceArena arena;
+  rt_alloc_fn alloc_fn = nullptr;
+  rt_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
+  DeviceArena shared;                 // descriptor array and work list
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  std::vector<Instance> inst;
-  InstDesc* d_desc = nullptr;
-  WorkItem* d_items = nullptr;        // capacity: all stage items of all problems
-  WorkItem* d_init_items = nullptr;
-  std::vector<int> init_offset;
-  std::vector<int64_t> done;          // steps enqueued per problem
-  int integrator = RT_EULER, storage = RT_FP32;
+  int storage = RT_FP32;
+  int tile_x = 0, tile_y = 0, variant = 0, vec = 0;
+  std::vector<Slot> slots;
+  InstDesc* d_desc = nullptr;         // [capacity]
+  WorkItem* d_items = nullptr;
+  size_t items_cap = 0;
+  // work list and graph of the current membership
+  bool dirty = true;
+  std::vector<Group> groups;
+  std::vector<int> members;           // slots in the current work list
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_n = 0;
   bool failed = false;
 };
 
-static rt_status batch_fail(rt_batch* b, rt_status st) {
+namespace {
+
+rt_status batch_fail(rt_batch* b, rt_status st) {
   if (b && st != RT_OK && st != RT_EINVAL) b->failed = true;
   return st;
 }
 
-static rt_status enqueue_phase_steps(rt_batch* b, const std::vector<Group>& groups, int64_t n, cudaStream_t stream) {
+void drop_graph(rt_batch* b) {
+  if (b->graph) {
+    cudaStreamSynchronize(b->stream);
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->graph_n = 0;
+}
+
+// Build, validate and initialise a problem in slot `i`.
+rt_status add_in_slot(rt_batch* b, const rt_problem& P, int i) {
+  Slot& S = b->slots[i];
+  S.arena.reset(new DeviceArena());
+  S.arena->alloc_fn = b->alloc_fn;
+  S.arena->free_fn = b->free_fn;
+  S.arena->ctx = b->alloc_ctx;
+  S.inst = Instance();
+  std::vector<std::vector<char>> keep;
+  const int ty = P.tile_y ? P.tile_y : b->tile_y;
+  const int var = P.variant ? P.variant : b->variant;
+  const int vec = P.vec ? P.vec : b->vec;
+  rt_status st = build_instance(&P.mesh, &P.mat, &P.quad, &P.bc, P.order, P.integrator, b->storage, P.dt, P.t_end,
+                                b->tile_x, ty, *S.arena, b->stream, S.inst, keep, var, vec);
+  auto undo = [&](rt_status code) {
+    cudaStreamSynchronize(b->stream);
+    (void)cudaGetLastError();
+    S.arena->free_all();
+    S.arena.reset();
+    S.used = false;
+    return code;
+  };
+  if (st != RT_OK) return undo(st);
+  Instance& I = S.inst;
+  void* p = nullptr;
+  if ((st = S.arena->get(I.init_items.size() * sizeof(WorkItem), &p)) != RT_OK) return undo(st);
+  S.d_init_items = (WorkItem*)p;
+  std::vector<WorkItem> hi = I.init_items;
+  for (WorkItem& w : hi) w.inst = 0;   // init launches are per problem (descriptor pointer offset by slot)
+  if (cudaMemcpyAsync(S.d_init_items, hi.data(), hi.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(b->d_desc + i, &I.desc, sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
+    set_error("copying a problem's descriptor failed");
+    return undo(RT_ECUDA);
+  }
+  if ((st = prepare_instance_kernels(I, I.ly)) != RT_OK) return undo(st);
+  cudaError_t e = launch_init(b->d_desc + i, S.d_init_items, (int)I.init_items.size(), I.vec, I.storage, b->stream);
+  if (e != cudaSuccess) {
+    set_error("init launch failed: %s", cudaGetErrorString(e));
+    return undo(RT_ECUDA);
+  }
+  InstState h;
+  if ((st = read_inst_state(I, b->stream, &h)) != RT_OK) return undo(st);
+  S.used = true;
+  S.done = 0;
+  b->dirty = true;
+  return RT_OK;
+}
+
+// Rebuild the work list of the unfinished problems, grouped by kernel variant.
+rt_status rebuild(rt_batch* b) {
+  drop_graph(b);
+  std::map<std::tuple<int, int, int, int, int, int, int>, std::vector<int>> by_variant;
+  b->members.clear();
+  for (int i = 0; i < (int)b->slots.size(); ++i) {
+    const Slot& S = b->slots[i];
+    if (!S.used || S.done >= S.inst.n_steps) continue;
+    const Instance& I = S.inst;
+    by_variant[std::make_tuple(I.kind, I.order, I.integrator, I.run, I.cvec, I.vec, I.uni)].push_back(i);
+    b->members.push_back(i);
+  }
+  std::vector<WorkItem> items;
+  b->groups.clear();
+  for (auto& kv : by_variant) {
+    Group g{};
+    std::tie(g.kind, g.order, g.integrator, g.run, g.cvec, g.vec, g.uni) = kv.first;
+    g.offset = (int)items.size();
+    g.ly_max = 1;
+    for (int i : kv.second) {
+      const Instance& I = b->slots[i].inst;
+      g.ly_max = std::max(g.ly_max, I.ly);
+      for (WorkItem w : I.stage_items) {
+        w.inst = i;
+        items.push_back(w);
+      }
+    }
+    g.count = (int)items.size() - g.offset;
+    rt_status pst = prepare_instance_kernels(b->slots[kv.second[0]].inst, g.ly_max);
+    if (pst != RT_OK) return pst;
+    b->groups.push_back(g);
+  }
+  if (items.size() > b->items_cap) {
+    cudaStreamSynchronize(b->stream);
+    if (b->d_items) b->shared.release(b->d_items);
+    b->d_items = nullptr;
+    b->items_cap = 0;
+    void* p = nullptr;
+    const size_t cap = std::max<size_t>(items.size() * 2, 1024);
+    rt_status st = b->shared.get(cap * sizeof(WorkItem), &p);
+    if (st != RT_OK) return st;
+    b->d_items = (WorkItem*)p;
+    b->items_cap = cap;
+  }
+  if (!items.empty()) {
+    cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the host list goes out of scope
+    if (e != cudaSuccess) {
+      set_error("copying the work list failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  }
+  b->dirty = false;
+  return RT_OK;
+}
+
+rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream) {
   for (int64_t i = 0; i < n; ++i) {
-    for (const Group& g : groups) {
-      rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, b->integrator, b->storage,
-                                 g.order, g.run, g.cvec, g.ly_max, g.vec, stream, g.uni);
+    for (const Group& g : b->groups) {
+      rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, g.integrator, b->storage, g.order,
+                                 g.run, g.cvec, g.ly_max, g.vec, stream, g.uni);
       if (st != RT_OK) return st;
     }
   }
   return RT_OK;
 }
 
+constexpr int64_t kGraphMinSteps = 4;
+
+rt_status step_members(rt_batch* b, int64_t n) {
+  if (b->dirty) {
+    rt_status st = rebuild(b);
+    if (st != RT_OK) return st;
+  }
+  if (b->members.empty() || n <= 0) return RT_OK;
+  if (n >= kGraphMinSteps) {
+    if (!b->graph || b->graph_n != n) {
+      drop_graph(b);
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        set_error("graph capture could not start");
+        return RT_ECUDA;
+      }
+      rt_status st = enqueue_steps(b, n, b->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (st != RT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st == RT_OK) set_error("graph capture failed: %s", cudaGetErrorString(e));
+        return st != RT_OK ? st : RT_ECUDA;
+      }
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+        return RT_ECUDA;
+      }
+      b->graph_n = n;
+    }
+    cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) {
+      set_error("graph launch failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  } else {
+    rt_status st = enqueue_steps(b, n, b->stream);
+    if (st != RT_OK) return st;
+  }
+  for (int i : b->members) {
+    Slot& S = b->slots[i];
+    S.done = std::min(S.inst.n_steps, S.done + n);
+    if (S.done >= S.inst.n_steps) b->dirty = true;   // drop it from the work list next time
+  }
+  return RT_OK;
+}
+
+bool slot_ok(const rt_batch* b, int32_t i) { return i >= 0 && i < (int)b->slots.size() && b->slots[i].used; }
+
+}  // namespace
+
 extern "C" {
 
-rt_status rt_batch_create(int32_t k, const rt_problem* problems, const rt_options* opts, rt_batch** out) {
+rt_status rt_batch_create(int32_t k, const rt_problem* problems, int32_t capacity, const rt_options* opts,
+                          rt_batch** out) {
   clear_error();
   if (!out) { set_error("out is NULL"); return RT_EINVAL; }
   *out = nullptr;
-  if (k < 1 || !problems || !opts) { set_error("need k >= 1, problems and options"); return RT_EINVAL; }
+  if (k < 0 || (k > 0 && !problems) || !opts) { set_error("need k >= 0, problems (when k > 0) and options"); return RT_EINVAL; }
+  if (capacity == 0) capacity = k;
+  if (capacity < k || capacity < 1 || capacity > (1 << 20)) { set_error("capacity must be in max(k,1)..2^20"); return RT_EINVAL; }
   if ((opts->alloc == nullptr) != (opts->free == nullptr)) { set_error("alloc and free must both be set or both NULL"); return RT_EINVAL; }
-  for (int i = 1; i < k; ++i)
-    if (problems[i].integrator != problems[0].integrator) { set_error("all problems of a batch must use the same integrator"); return RT_EINVAL; }
+  if (opts->storage != RT_FP32 && opts->storage != RT_BF16) { set_error("storage must be RT_FP32 or RT_BF16"); return RT_EINVAL; }
   rt_batch* b = new rt_batch();
-  b->arena.alloc_fn = opts->alloc;
-  b->arena.free_fn = opts->free;
-  b->arena.ctx = opts->alloc_ctx;
+  b->alloc_fn = opts->alloc;
+  b->free_fn = opts->free;
+  b->alloc_ctx = opts->alloc_ctx;
+  b->shared.alloc_fn = opts->alloc;
+  b->shared.free_fn = opts->free;
+  b->shared.ctx = opts->alloc_ctx;
   b->stream = (cudaStream_t)opts->stream;
-  b->integrator = problems[0].integrator;
   b->storage = opts->storage;
-  b->inst.resize(k);
-  b->done.assign(k, 0);
+  b->tile_x = opts->tile_x;
+  b->tile_y = opts->tile_y;
+  b->variant = opts->variant;
+  b->vec = opts->vec;
+  b->slots.resize(capacity);
   auto bail = [&](rt_status code) {
     cudaStreamSynchronize(b->stream);
     (void)cudaGetLastError();
-    b->arena.free_all();
+    for (Slot& S : b->slots)
+      if (S.arena) S.arena->free_all();
+    b->shared.free_all();
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return code;
   };
-  std::vector<std::vector<char>> keep;
-  size_t n_stage = 0, n_init = 0;
-  for (int i = 0; i < k; ++i) {
-    const rt_problem& P = problems[i];
-    rt_status st = build_instance(&P.mesh, &P.mat, &P.quad, &P.bc, P.order, P.integrator, opts->storage, P.dt,
-                                  P.t_end, opts->tile_x, opts->tile_y, b->arena, b->stream, b->inst[i], keep,
-                                  opts->variant);
-    if (st != RT_OK) {
-      char msg[1200];
-      snprintf(msg, sizeof(msg), "problem %d: %s", i, rt_last_error());
-      set_error("%s", msg);
-      return bail(st);
-    }
-    n_stage += b->inst[i].stage_items.size();
-    b->init_offset.push_back((int)n_init);
-    n_init += b->inst[i].init_items.size();
-    // host copies of per-problem arrays are already on the stream; sync to bound host memory
-    if (keep.size() > 64) {
-      if (cudaStreamSynchronize(b->stream) != cudaSuccess) { set_error("stream failed during create"); return bail(RT_ECUDA); }
-      keep.clear();
-    }
-  }
   void* p = nullptr;
-  rt_status st;
-  if ((st = b->arena.get((size_t)k * sizeof(InstDesc), &p)) != RT_OK) return bail(st);
+  rt_status st = b->shared.get((size_t)capacity * sizeof(InstDesc), &p);
+  if (st != RT_OK) return bail(st);
   b->d_desc = (InstDesc*)p;
-  if ((st = b->arena.get(n_stage * sizeof(WorkItem), &p)) != RT_OK) return bail(st);
-  b->d_items = (WorkItem*)p;
-  if ((st = b->arena.get(n_init * sizeof(WorkItem), &p)) != RT_OK) return bail(st);
-  b->d_init_items = (WorkItem*)p;
-  std::vector<InstDesc> hd(k);
-  std::vector<WorkItem> hi;
-  hi.reserve(n_init);
-  for (int i = 0; i < k; ++i) {
-    hd[i] = b->inst[i].desc;
-    for (WorkItem w : b->inst[i].init_items) {
-      w.inst = 0;   // init launches are per problem (descriptor pointer offset by i)
-      hi.push_back(w);
-    }
-  }
-  if (cudaMemcpyAsync(b->d_desc, hd.data(), (size_t)k * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(b->d_init_items, hi.data(), hi.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, b->stream) != cudaSuccess) {
-    set_error("copying batch descriptors failed");
+  if (cudaMemsetAsync(b->d_desc, 0, (size_t)capacity * sizeof(InstDesc), b->stream) != cudaSuccess) {
+    set_error("clearing the descriptor array failed");
     return bail(RT_ECUDA);
-  }
-  for (int i = 0; i < k; ++i) {
-    const Instance& I = b->inst[i];
-    if ((st = prepare_instance_kernels(I, I.ly)) != RT_OK) return bail(st);
-    cudaError_t e = launch_init(b->d_desc + i, b->d_init_items + b->init_offset[i], (int)I.init_items.size(), I.vec,
-                                I.storage, b->stream);
-    if (e != cudaSuccess) {
-      set_error("init launch failed: %s", cudaGetErrorString(e));
-      return bail(RT_ECUDA);
-    }
-  }
-  for (int i = 0; i < k; ++i) {
-    InstState h;
-    if ((st = read_inst_state(b->inst[i], b->stream, &h)) != RT_OK) return bail(st);
   }
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     set_error("stream creation failed");
     return bail(RT_ECUDA);
   }
+  for (int i = 0; i < k; ++i) {
+    if ((st = add_in_slot(b, problems[i], i)) != RT_OK) {
+      char msg[1200];
+      snprintf(msg, sizeof(msg), "problem %d: %s", i, rt_last_error());
+      set_error("%s", msg);
+      return bail(st);
+    }
+  }
   *out = b;
   return RT_OK;
+}
+
+rt_status rt_batch_add(rt_batch* b, const rt_problem* problem, int32_t* slot) {
+  clear_error();
+  if (!b || !problem || !slot) { set_error("batch, problem and slot are required"); return RT_EINVAL; }
+  if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
+  int i = 0;
+  while (i < (int)b->slots.size() && b->slots[i].used) ++i;
+  if (i == (int)b->slots.size()) { set_error("no free slot (capacity %d)", (int)b->slots.size()); return RT_EINVAL; }
+  rt_status st = add_in_slot(b, *problem, i);
+  if (st != RT_OK) return st == RT_ECUDA ? batch_fail(b, st) : st;
+  *slot = i;
+  return RT_OK;
+}
+
+rt_status rt_batch_remove(rt_batch* b, int32_t i) {
+  clear_error();
+  if (!b) { set_error("batch is NULL"); return RT_EINVAL; }
+  if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
+  drop_graph(b);
+  cudaStreamSynchronize(b->stream);
+  Slot& S = b->slots[i];
+  S.arena->free_all();
+  S.arena.reset();
+  S.used = false;
+  S.done = 0;
+  b->dirty = true;
+  return RT_OK;
+}
+
+rt_status rt_batch_step(rt_batch* b, int64_t n) {
+  clear_error();
+  if (!b) { set_error("batch is NULL"); return RT_EINVAL; }
+  if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
+  if (n < 0) { set_error("n must be >= 0"); return RT_EINVAL; }
+  rt_status st = step_members(b, n);
+  return st == RT_OK ? RT_OK : batch_fail(b, st);
 }
 
 rt_status rt_batch_run(rt_batch* b, int64_t max_steps) {
   clear_error();
   if (!b) { set_error("batch is NULL"); return RT_EINVAL; }
   if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
-  const int k = (int)b->inst.size();
-  std::vector<int64_t> target(k);
-  for (int i = 0; i < k; ++i) {
-    target[i] = b->inst[i].n_steps;
-    if (max_steps > 0) target[i] = std::min(target[i], b->done[i] + max_steps);
-  }
-  while (true) {
+  constexpr int64_t kChunkSteps = 8;
+  int64_t budget = max_steps > 0 ? max_steps : INT64_MAX;
+  while (budget > 0) {
+    // steps until the next problem finishes
     int64_t phase = INT64_MAX;
-    for (int i = 0; i < k; ++i)
-      if (b->done[i] < target[i]) phase = std::min(phase, target[i] - b->done[i]);
+    for (const Slot& S : b->slots)
+      if (S.used && S.done < S.inst.n_steps) phase = std::min(phase, S.inst.n_steps - S.done);
     if (phase == INT64_MAX) break;
-    // work list of the unfinished problems, grouped by kernel variant
-    std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> by_variant;
-    for (int i = 0; i < k; ++i) {
-      if (b->done[i] >= target[i]) continue;
-      const Instance& I = b->inst[i];
-      by_variant[std::make_tuple(I.kind, I.order, I.run, I.cvec, I.vec, I.uni)].push_back(i);
-    }
-    std::vector<WorkItem> items;
-    std::vector<Group> groups;
-    for (auto& kv : by_variant) {
-      Group g{};
-      std::tie(g.kind, g.order, g.run, g.cvec, g.vec, g.uni) = kv.first;
-      g.offset = (int)items.size();
-      g.ly_max = 1;
-      for (int i : kv.second) {
-        const Instance& I = b->inst[i];
-        g.ly_max = std::max(g.ly_max, I.ly);
-        for (WorkItem w : I.stage_items) {
-          w.inst = i;
-          items.push_back(w);
-        }
-      }
-      g.count = (int)items.size() - g.offset;
-      groups.push_back(g);
-      rt_status pst = prepare_instance_kernels(b->inst[kv.second[0]], g.ly_max);
-      if (pst != RT_OK) return batch_fail(b, pst);
-    }
-    cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
-                                    b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the host list is freed at the end of the phase
-    if (e != cudaSuccess) {
-      set_error("copying the work list failed: %s", cudaGetErrorString(e));
-      return batch_fail(b, RT_ECUDA);
-    }
+    phase = std::min(phase, budget);
     int64_t left = phase;
-    if (phase >= 2 * kBatchGraphSteps) {
-      cudaGraph_t g = nullptr;
-      cudaGraphExec_t ge = nullptr;
-      if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        set_error("graph capture could not start");
-        return batch_fail(b, RT_ECUDA);
-      }
-      rt_status st = enqueue_phase_steps(b, groups, kBatchGraphSteps, b->cap_stream);
-      e = cudaStreamEndCapture(b->cap_stream, &g);
-      if (st != RT_OK || e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        if (st == RT_OK) set_error("graph capture failed: %s", cudaGetErrorString(e));
-        return batch_fail(b, st != RT_OK ? st : RT_ECUDA);
-      }
-      e = cudaGraphInstantiate(&ge, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        set_error("graph instantiation failed: %s", cudaGetErrorString(e));
-        return batch_fail(b, RT_ECUDA);
-      }
-      while (left >= kBatchGraphSteps) {
-        e = cudaGraphLaunch(ge, b->stream);
-        if (e != cudaSuccess) break;
-        left -= kBatchGraphSteps;
-      }
-      // keep the executable graph alive until its replays have been consumed
-      cudaError_t e2 = cudaStreamSynchronize(b->stream);
-      cudaGraphExecDestroy(ge);
-      if (e != cudaSuccess || e2 != cudaSuccess) {
-        set_error("graph replay failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-        return batch_fail(b, RT_ECUDA);
-      }
+    while (left > 0) {
+      const int64_t n = left >= kChunkSteps ? kChunkSteps : left;
+      rt_status st = step_members(b, n);
+      if (st != RT_OK) return batch_fail(b, st);
+      left -= n;
     }
-    rt_status st = enqueue_phase_steps(b, groups, left, b->stream);
-    if (st != RT_OK) return batch_fail(b, st);
-    for (int i = 0; i < k; ++i)
-      if (b->done[i] < target[i]) b->done[i] += phase;
+    budget -= phase;
   }
+  return RT_OK;
+}
+
+rt_status rt_batch_progress(const rt_batch* b, int32_t i, int64_t* steps_done, int64_t* n_steps) {
+  clear_error();
+  if (!b) { set_error("batch is NULL"); return RT_EINVAL; }
+  if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
+  if (steps_done) *steps_done = b->slots[i].done;
+  if (n_steps) *n_steps = b->slots[i].inst.n_steps;
   return RT_OK;
 }
 
 rt_status rt_batch_qoi(rt_batch* b, int32_t i, rt_qoi_t* out) {
   clear_error();
   if (!b || !out) { set_error("batch and out are required"); return RT_EINVAL; }
-  if (i < 0 || i >= (int)b->inst.size()) { set_error("problem index %d out of range", i); return RT_EINVAL; }
+  if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
   if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
   InstState h;
-  rt_status st = read_inst_state(b->inst[i], b->stream, &h);
+  rt_status st = read_inst_state(b->slots[i].inst, b->stream, &h);
   if (st != RT_OK) return batch_fail(b, st);
-  fill_qoi(b->inst[i], h, out);
+  fill_qoi(b->slots[i].inst, h, out);
   return RT_OK;
 }
 
 rt_status rt_batch_get_psi(rt_batch* b, int32_t i, double* host, int64_t n) {
   clear_error();
   if (!b || !host) { set_error("batch and host are required"); return RT_EINVAL; }
-  if (i < 0 || i >= (int)b->inst.size()) { set_error("problem index %d out of range", i); return RT_EINVAL; }
+  if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
   if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
-  const Instance& I = b->inst[i];
+  Slot& S = b->slots[i];
+  const Instance& I = S.inst;
   if (n != I.n_cells * I.M) { set_error("n must be n_cells*M = %lld", (long long)(I.n_cells * I.M)); return RT_EINVAL; }
   InstState h;
   rt_status st = read_inst_state(I, b->stream, &h);
   if (st != RT_OK) return batch_fail(b, st);
-  st = copy_psi_out(I, b->arena, b->stream, h.parity, host);
+  st = copy_psi_out(I, *S.arena, b->stream, h.parity, host);
   return st == RT_OK ? RT_OK : batch_fail(b, st);
 }
 
@@ -272,8 +408,11 @@ void rt_batch_destroy(rt_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   (void)cudaGetLastError();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  b->arena.free_all();
+  for (Slot& S : b->slots)
+    if (S.arena) S.arena->free_all();
+  b->shared.free_all();
   delete b;
 }
 

@@ -3,7 +3,8 @@
 #include "cart_kernel.cuh"
 
 namespace rtk {
-#define RTK_CART_UNIT_LIST(X, TT, U) RTK_CART_STAGES(X, 1, 2, U, TT) RTK_CART_STAGES(X, 1, 4, U, TT) RTK_CART_STAGES(X, 2, 2, U, TT) RTK_CART_STAGES(X, 2, 4, U, TT)
+#define RTK_CART_UNIT_LIST(X, TT, U) RTK_CART_STAGES(X, 1, 2, 2, U, TT) RTK_CART_STAGES(X, 1, 2, 4, U, TT) \
+  RTK_CART_STAGES(X, 2, 2, 2, U, TT) RTK_CART_STAGES(X, 2, 2, 4, U, TT)
 RTK_CART_DEFINE_UNIT(f32_uni, float, true)
 #undef RTK_CART_UNIT_LIST
 }  // namespace rtk

@@ -33,6 +33,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace rtk {
@@ -124,6 +126,70 @@ __device__ __forceinline__ void stg_vec(T* p, const float (&in)[V]) {
       *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(in[0], in[1]);
     } else {
       *p = __float2bfloat16_rn(in[0]);
+    }
+  }
+}
+
+// ---- paired FP32 helpers (two values per instruction on sm_100 and later)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);   // a - b, rounded once
+}
+__device__ __forceinline__ float2 minmod2(float2 a, float2 b) {
+  return make_float2(minmod_med(a.x, b.x), minmod_med(a.y, b.y));
+}
+__device__ __forceinline__ float2 relu2(float2 a) { return make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)); }
+// minmod(a, b) = min(max(a, b), max(a, 0), max(b, 0)), the last two given: for
+// a <= b this is a when 0 <= a, 0 when a < 0 <= b and b when b < 0, i.e. the
+// median of (a, b, 0). A difference feeds two faces, so its max(., 0) is shared.
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float2 minmod2r(float2 a, float2 b, float2 ra, float2 rb) {
+  return make_float2(fmin3f(fmaxf(a.x, b.x), ra.x, rb.x), fmin3f(fmaxf(a.y, b.y), ra.y, rb.y));
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void lds_vec2(const T* p, float2 (&out)[V / 2]) {
+  static_assert(V == 2 || V == 4, "pairs need V = 2 or 4");
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (V == 4) {
+      const float4 x = *reinterpret_cast<const float4*>(p);
+      out[0] = make_float2(x.x, x.y);
+      out[1] = make_float2(x.z, x.w);
+    } else {
+      out[0] = *reinterpret_cast<const float2*>(p);
+    }
+  } else {
+    if constexpr (V == 4) {
+      const uint2 x = *reinterpret_cast<const uint2*>(p);
+      out[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x.x));
+      out[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x.y));
+    } else {
+      out[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+  }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stg_vec2(T* p, const float2 (&in)[V / 2]) {
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (V == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(in[0].x, in[0].y, in[1].x, in[1].y);
+    } else {
+      *reinterpret_cast<float2*>(p) = in[0];
+    }
+  } else {
+    if constexpr (V == 4) {
+      __nv_bfloat162 a = __floats2bfloat162_rn(in[0].x, in[0].y);
+      __nv_bfloat162 b = __floats2bfloat162_rn(in[1].x, in[1].y);
+      uint2 x;
+      x.x = *reinterpret_cast<uint32_t*>(&a);
+      x.y = *reinterpret_cast<uint32_t*>(&b);
+      *reinterpret_cast<uint2*>(p) = x;
+    } else {
+      *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(in[0].x, in[0].y);
     }
   }
 }
@@ -459,6 +525,38 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
   cart_epilogue<TX, STAGE>(d, it, phi_out, tile_acc, red, x0, ya, nrows, bacc);
 }
 
+// One row pull of the chunk-uniform tile: pull e (chunk c, row i of the chunk)
+// into ring slot `slot`, completing full[slot].
+template <typename L>
+struct UniPull {
+  const InstDesc* d;
+  uint8_t* ring;
+  uint64_t* full;
+  int* slot_pull;   // [NS] last pull issued into each slot (read by the drain)
+  const CUtensorMap* map_halo;
+  const CUtensorMap* map_base;
+  int x0, ya, yb;
+
+  __device__ __forceinline__ void issue(int e, int c, int i, int slot) const {
+    constexpr int H = L::H, C = L::C;
+    const int dy = d->cdir_y[c];
+    const int p = ((dy > 0) ? ya : yb - 1) + dy * (i - H);
+    uint8_t* dst = ring + slot * L::slot_bytes;
+    const bool halo = (p >= 0 && p < d->ny);
+    const bool base = L::base_bytes > 0 && (i >= H + 1);   // Heun stage 2: psi^n of the row completed here
+    const uint32_t bytes = (halo ? L::halo_bytes : 0) + (base ? L::base_bytes : 0);
+    slot_pull[slot] = e;
+    if ((int64_t)e == d->drop_load) return;   // test hook: that pull never completes
+    if (bytes == 0) {
+      mbar_arrive(&full[slot]);
+      return;
+    }
+    mbar_arrive_expect_tx(&full[slot], bytes);
+    if (halo) tma_load_3d(dst, map_halo, &full[slot], c * C, x0 - H, p);
+    if (base) tma_load_3d(dst + L::halo_bytes, map_base, &full[slot], c * C, x0, p - dy);
+  }
+};
+
 // Chunk-uniform variant. When every chunk of C ordinates has one sign of xi and
 // one of eta (the product quadrature's quadrants are contiguous, so its chunks
 // are), the whole CTA shares the flow direction of a chunk. Each chunk then
@@ -466,11 +564,22 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
 // consecutive rows comes from the row already seen, so a row is completed one
 // row after it arrives, and the window carries only the previous row, its
 // difference to the row before, and the face value below it.
+//
+// Pipeline. Pull q of the tile (all chunks in order) lands in ring slot q mod NS
+// and completes full[slot]. Pull q - 1 is needed until every warp has finished
+// pull q; after the CTA barrier that closes row q, thread 0 issues pull
+// q - 1 + NS into its slot. (Releasing slots per warp with shared-memory
+// atomics or mbarrier arrivals, so that warps run apart, measured slower on
+// sm_103a than this one barrier per row.) The waits are bounded; the barrier
+// also carries a failed wait, so all warps stop together, drain the loads in
+// flight and report the timeout.
 template <int ORDER, int R, int V, int STAGE, typename T, bool XB>
 __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem& it, InstState* st,
                                               uint8_t* smem, const bool YB) {
   using L = CartCfg<ORDER, R, V, STAGE, T>;
   constexpr int H = L::H, TX = L::TX, C = L::C, NS = L::NS, NL = L::NL;
+  constexpr int V2 = V / 2;   // ordinate pairs per lane: arithmetic runs on float pairs
+  static_assert(NS >= 3, "the ring must hold two resident rows plus one load in flight");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const int parity = (STAGE == STAGE_EULER) ? st->parity : 0;
@@ -491,39 +600,20 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   const int total = d.n_chunks * Lc;
 
   uint8_t* ring = smem;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::ring_bytes);
-  float* tile_a = reinterpret_cast<float*>(smem + L::ring_bytes + 128);
-  float* tile_b = tile_a + d.ly * TX;
-  float* tile_acc = tile_b + d.ly * TX;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::ring_bytes);
+  int* slot_pull = reinterpret_cast<int*>(full + NS);   // [NS]
+  float2* tile_ab = reinterpret_cast<float2*>(smem + L::ring_bytes + 128);   // (a, b) per cell
+  float* tile_acc = reinterpret_cast<float*>(tile_ab + d.ly * TX);
   double* red = reinterpret_cast<double*>(smem + L::ring_bytes + 128 + cart_tile_bytes(TX, d.ly));
   const int64_t limit = d.wait_limit;
-
-  // row of pull i of chunk c: the tile rows in flow order, with H rows before and one after
-  auto pull_row = [&](int c, int i) {
-    const int dy = d.cdir_y[c];
-    return ((dy > 0) ? ya : yb - 1) + dy * (i - H);
-  };
-  auto issue = [&](int q) {
-    const int slot = q % NS;
-    const int c = q / Lc;
-    const int i = q - c * Lc;
-    const int p = pull_row(c, i);
-    uint8_t* dst = ring + slot * L::slot_bytes;
-    const bool halo = (p >= 0 && p < ny);
-    const bool base = (STAGE == STAGE_HEUN2) && (i >= H + 1);   // the row completed at this pull
-    const uint32_t bytes = (halo ? L::halo_bytes : 0) + (base ? L::base_bytes : 0);
-    if ((int64_t)q == d.drop_load) return;   // test hook: this slot never completes
-    if (bytes == 0) {
-      mbar_arrive(&bars[slot]);
-      return;
-    }
-    mbar_arrive_expect_tx(&bars[slot], bytes);
-    if (halo) tma_load_3d(dst, map_halo, &bars[slot], c * C, x0 - H, p);
-    if (base) tma_load_3d(dst + L::halo_bytes, map_base, &bars[slot], c * C, x0, p - d.cdir_y[c]);
-  };
+  static_assert(NS * (8 + 4) <= 128, "ring control block must fit its 128 bytes");
+  const UniPull<L> pull{&d, ring, full, slot_pull, map_halo, map_base, x0, ya, yb};
 
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      slot_pull[s] = -1;
+    }
     fence_barrier_init();
     fence_tensormap_acquire(map_halo);
     prefetch_tensormap(map_halo);
@@ -534,7 +624,10 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   }
   __syncthreads();
   if (tid == 0) {
-    for (int q = 0; q < min(NS, total); ++q) issue(q);
+    for (int e = 0, c = 0, i = 0; e < min(NS, total); ++e) {
+      pull.issue(e, c, i, e);
+      if (++i == Lc) { i = 0; ++c; }
+    }
   }
   const float dt = d.dt;
   for (int i = tid; i < nrows * TX; i += kCartThreads) {
@@ -547,8 +640,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
       a = 1.f - dt * d.sig_t[m];
       b = dt * (d.sig_s2pi[m] * phi_in[cell] + d.q_src[m]);
     }
-    tile_a[i] = a;
-    tile_b[i] = b;
+    tile_ab[i] = make_float2(a, b);
     tile_acc[i] = 0.f;
   }
   __syncthreads();
@@ -556,184 +648,233 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   float bacc = 0.f;
   const float ly_f = (float)d.dy_d, lx_f = (float)d.dx_d;
   const int xl0 = warp * R;
-  static_assert(NS >= 3, "the ring must hold two resident rows plus one load in flight");
+  bool ok = true;
+  int q = 0;           // global pull index
+  int slot = 0;        // ring slot of pull q
+  uint32_t ph = 0;     // phase parity of full[slot] for pull q
+  int pslot = NS - 1;  // ring slot of pull q - 1
+  // chunk and row of pull q - 1 + NS, issued after row q (advanced once per pull from q = 1)
+  int nc = 0, ni = NS;
+  while (ni >= Lc) { ni -= Lc; ++nc; }
 
-  int q = 0;
-  int issued = min(NS, total);
-  for (int c = 0; c < d.n_chunks; ++c) {
-    const int k0 = c * C + lane * V;
-    const int dxs = d.cdir_x[c], dys = d.cdir_y[c];     // uniform over the CTA
-    const int s0 = (dxs > 0) ? xl0 : xl0 + R - 1;
-    float w[V], ax[V], ay[V];
+  for (int c = 0; c < d.n_chunks && ok; ++c) {
+    auto chunk = [&](auto dir) {
+      constexpr int DXS = decltype(dir)::value;   // sign of xi in this chunk
+      const int k0 = c * C + lane * V;
+      const int dys = d.cdir_y[c];
+      const int s0 = (DXS > 0) ? xl0 : xl0 + R - 1;   // this warp's first cell along the flow
+      float2 w2[V2], ax2[V2], ay2[V2];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      w[v] = d.w[k0 + v];
-      ax[v] = dt * fabsf(d.xi[k0 + v]) * d.inv_dx;
-      ay[v] = dt * fabsf(d.eta[k0 + v]) * d.inv_dy;
-    }
-    // psi^- of the rows before the tile in flow order (entering through that side)
-    const float gy_up = (dys > 0) ? d.ghost[2] : d.ghost[3];
-    const int start = (dys > 0) ? ya : yb - 1;
-    float cm1[R][V], dprev[R][V], gprev[R][V];
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int v = 0; v < V; ++v) cm1[r][v] = dprev[r][v] = gprev[r][v] = 0.f;
+      for (int v = 0; v < V2; ++v) {
+        w2[v] = make_float2(d.w[k0 + 2 * v], d.w[k0 + 2 * v + 1]);
+        ax2[v] = make_float2(dt * fabsf(d.xi[k0 + 2 * v]) * d.inv_dx, dt * fabsf(d.xi[k0 + 2 * v + 1]) * d.inv_dx);
+        ay2[v] = make_float2(dt * fabsf(d.eta[k0 + 2 * v]) * d.inv_dy, dt * fabsf(d.eta[k0 + 2 * v + 1]) * d.inv_dy);
+      }
+      // psi^- of the rows before the tile in flow order (entering through that side)
+      const float gy_up = (dys > 0) ? d.ghost[2] : d.ghost[3];
+      const int start = (dys > 0) ? ya : yb - 1;
+      // lane's element of cell position s0 within a slot, in bytes
+      const int lofs = ((s0 + H) * C + lane * V) * (int)sizeof(T);
+      constexpr int PSTEP = DXS * C * (int)sizeof(T);   // next cell along the flow
+      // output row pointer (row `start`, cell s0) and its step per completed row
+      T* op = psi_out + ((size_t)start * nx + (x0 + s0)) * Mpad + k0;
+      const ptrdiff_t ostep = (ptrdiff_t)dys * nx * Mpad;
+      const ptrdiff_t mstep = (ptrdiff_t)DXS * Mpad;
+      const float2* tab = tile_ab + (start - ya) * TX + s0;
+      const int tstep = dys * TX;
+      float* tacc = tile_acc + (start - ya) * TX + xl0 + lane / (32 / R);
+      int jrow = start;    // row completed next
 
-    for (int i = 0; i < Lc; ++i, ++q) {
-      const int p = start + dys * (i - H);
-      const int slot = q % NS;
-      const uint32_t par = (uint32_t)((q / NS) & 1);
-      const bool ok = mbar_wait_bounded(&bars[slot], par, limit);
-      const T* srow = reinterpret_cast<const T*>(ring + slot * L::slot_bytes);
-      float c0[R][V];
-      const bool p_in = (p >= 0 && p < ny);
-      if (YB && !p_in) {
-        const float gv = (i < H) ? gy_up : 0.f;   // after the tile only the first-order face sees it
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int v = 0; v < V; ++v) c0[r][v] = gv;
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) lds_vec<T, V>(srow + (s0 + dxs * r + H) * C + lane * V, c0[r]);
-      }
-      // face between the previous row (upwind) and row p
-      float g[R][V];
-      if constexpr (ORDER == 2) {
-        float h = 0.5f;
-        if (YB) {
-          const int pp = p - dys;
-          const bool in_prev = (pp >= 0 && pp < ny);
-          if (in_prev != p_in) h = 0.f;   // domain boundary face: first order
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const float dn = c0[r][v] - cm1[r][v];
-            g[r][v] = fmaf(h, minmod_med(dn, dprev[r][v]), cm1[r][v]);
-            dprev[r][v] = dn;
-          }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int v = 0; v < V; ++v) g[r][v] = cm1[r][v];
-      }
-      // completion of the previous row j (its slot, entry q - 1, is still resident)
-      if (i >= H + 1) {
-        const int j = p - dys;
-        const int rr = j - ya;
-        const T* jrow = reinterpret_cast<const T*>(ring + ((q - 1) % NS) * L::slot_bytes);
-        const T* sbase = reinterpret_cast<const T*>(ring + slot * L::slot_bytes + L::halo_bytes);
-        float u[NL][V];
-#pragma unroll
-        for (int m = 0; m < NL; ++m) {
-          const int pos = s0 + dxs * (m - H);
-          lds_vec<T, V>(jrow + (pos + H) * C + lane * V, u[m]);
-          if constexpr (XB) {
-            const int gpos = x0 + pos;
-            if (gpos < 0 || gpos >= nx) {
-#pragma unroll
-              for (int v = 0; v < V; ++v) {
-                const float xiv = d.xi[k0 + v];
-                u[m][v] = (gpos < 0) ? ((xiv > 0.f) ? d.ghost[0] : 0.f) : ((xiv < 0.f) ? d.ghost[1] : 0.f);
-              }
-            }
-          }
-        }
-        float F[R + 1][V];
-#pragma unroll
-        for (int m = -1; m < R; ++m) {
-          float hx = (ORDER == 2) ? 0.5f : 0.f;
-          if constexpr (XB) {
-            const int ga = x0 + s0 + dxs * m, gb = ga + dxs;
-            if (!((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) hx = 0.f;
-          }
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const float um = u[m + H][v];
-            if constexpr (ORDER == 2) {
-              F[m + 1][v] = fmaf(hx, minmod_med(u[m + H + 1][v] - um, um - u[m + H - 1][v]), um);
-            } else {
-              F[m + 1][v] = um;
-            }
-          }
-        }
-        float contrib[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int xl = s0 + dxs * r;
-          const int gx = x0 + xl;
-          const float ta = tile_a[rr * TX + xl], tb = tile_b[rr * TX + xl];
-          float bse[V];
-          if constexpr (STAGE == STAGE_HEUN2) lds_vec<T, V>(sbase + xl * C + lane * V, bse);
-          float out[V];
-          float pw = 0.f;
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const float div = fmaf(ax[v], F[r + 1][v] - F[r][v], ay[v] * (g[r][v] - gprev[r][v]));
-            float t = fmaf(ta, cm1[r][v], tb) - div;
-            if constexpr (STAGE == STAGE_HEUN2) t = 0.5f * (bse[v] + t);
-            t = Store<T>::round(t);
-            out[v] = t;
-            pw = fmaf(w[v], t, pw);
-          }
-          contrib[r] = 0.f;
-          if (!XB || gx < nx) {
-            stg_vec<T, V>(psi_out + ((size_t)j * nx + gx) * Mpad + k0, out);
-            contrib[r] = pw;
-            if (XB || YB) {
-#pragma unroll
-              for (int v = 0; v < V; ++v) {
-                const float o = out[v], xiv = d.xi[k0 + v], etav = d.eta[k0 + v];
-                if (XB && gx == 0) bacc += ly_f * (w[v] * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
-                if (XB && gx == nx - 1) bacc += ly_f * (w[v] * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
-                if (YB && j == 0) bacc += lx_f * (w[v] * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
-                if (YB && j == ny - 1) bacc += lx_f * (w[v] * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
-              }
-            }
-          }
-        }
-        float phys[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) phys[r] = (dxs > 0) ? contrib[r] : contrib[R - 1 - r];
-        const float sphi = multi_warp_sum<R>(phys, lane);
-        if ((lane & (32 / R - 1)) == 0) tile_acc[rr * TX + xl0 + lane / (32 / R)] += sphi;
-      }
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-          for (int qq = q; qq < issued; ++qq) {
-            if ((int64_t)qq == d.drop_load) continue;
-            mbar_wait_bounded(&bars[qq % NS], (uint32_t)((qq / NS) & 1), limit);
-          }
-          atomicCAS(&st->status, DEV_OK, DEV_TIMEOUT);
-          st->timeout_where = ((int64_t)blockIdx.x << 32) | (int64_t)q;
-        }
-        return;
-      }
-      // entry q - 1 is consumed: its slot takes entry q - 1 + NS
-      if (tid == 0 && q >= 1 && issued < total) {
-        fence_proxy_async_smem();
-        issue(issued);
-        ++issued;
-      }
+      float2 cm1[R][V2], dprev[R][V2], rprev[R][V2], gprev[R][V2];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          gprev[r][v] = g[r][v];
-          cm1[r][v] = c0[r][v];
+        for (int v = 0; v < V2; ++v) cm1[r][v] = dprev[r][v] = rprev[r][v] = gprev[r][v] = make_float2(0.f, 0.f);
+
+      int p = start - dys * H;
+      for (int i = 0; i < Lc; ++i, ++q, p += dys) {
+        const bool wok = mbar_wait_bounded(&full[slot], ph, limit);
+        const uint8_t* cur = ring + slot * L::slot_bytes + lofs;
+        float2 c0[R][V2];
+        const bool p_in = (p >= 0 && p < ny);
+        if (YB && !p_in) {
+          const float gv = (i < H) ? gy_up : 0.f;   // after the tile only the first-order face sees it
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int v = 0; v < V2; ++v) c0[r][v] = make_float2(gv, gv);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) lds_vec2<T, V>(reinterpret_cast<const T*>(cur + r * PSTEP), c0[r]);
         }
-    }
+        // face between the previous row (upwind) and row p
+        float2 g[R][V2];
+        if constexpr (ORDER == 2) {
+          bool second = true;
+          if (YB) {
+            const int pp = p - dys;
+            if ((pp >= 0 && pp < ny) != p_in) second = false;   // domain boundary face: first order
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int v = 0; v < V2; ++v) {
+              const float2 dn = sub2(c0[r][v], cm1[r][v]);
+              const float2 rn = relu2(dn);
+              g[r][v] = second ? __ffma2_rn(make_float2(0.5f, 0.5f), minmod2r(dn, dprev[r][v], rn, rprev[r][v]),
+                                            cm1[r][v])
+                               : cm1[r][v];
+              dprev[r][v] = dn;
+              rprev[r][v] = rn;
+            }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int v = 0; v < V2; ++v) g[r][v] = cm1[r][v];
+        }
+        // completion of the previous row (its slot, pull q - 1, is still resident)
+        if (i >= H + 1) {
+          const uint8_t* prv = ring + pslot * L::slot_bytes + lofs;
+          float2 u[NL][V2];
+#pragma unroll
+          for (int m = 0; m < NL; ++m) {
+            lds_vec2<T, V>(reinterpret_cast<const T*>(prv + (m - H) * PSTEP), u[m]);
+            if constexpr (XB) {
+              const int gpos = x0 + s0 + DXS * (m - H);
+              if (gpos < 0 || gpos >= nx) {
+#pragma unroll
+                for (int v = 0; v < V2; ++v) {
+                  // entering ordinates see psi^- of the side, leaving ones nothing (only
+                  // first-order faces read it)
+                  const float gside = (gpos < 0) ? d.ghost[0] : d.ghost[1];
+                  const bool enter = (gpos < 0) == (DXS > 0);
+                  u[m][v] = enter ? make_float2(gside, gside) : make_float2(0.f, 0.f);
+                }
+              }
+            }
+          }
+          // faces m = -1 .. R-1 along x (outgoing face of upwind cell m); first order on domain faces
+          float2 F[R + 1][V2];
+          if constexpr (ORDER == 2) {
+            float2 D[NL][V2], RD[NL][V2];   // D[m] = u[m] - u[m-1], RD = max(D, 0)
+#pragma unroll
+            for (int m = 1; m < NL; ++m)
+#pragma unroll
+              for (int v = 0; v < V2; ++v) {
+                D[m][v] = sub2(u[m][v], u[m - 1][v]);
+                RD[m][v] = relu2(D[m][v]);
+              }
+#pragma unroll
+            for (int m = -1; m < R; ++m) {
+              bool second = true;
+              if constexpr (XB) {
+                const int ga = x0 + s0 + DXS * m, gb = ga + DXS;
+                if (!((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) second = false;
+              }
+#pragma unroll
+              for (int v = 0; v < V2; ++v)
+                F[m + 1][v] = second ? __ffma2_rn(make_float2(0.5f, 0.5f),
+                                                  minmod2r(D[m + H + 1][v], D[m + H][v], RD[m + H + 1][v], RD[m + H][v]),
+                                                  u[m + H][v])
+                                     : u[m + H][v];
+            }
+          } else {
+#pragma unroll
+            for (int m = -1; m < R; ++m)
+#pragma unroll
+              for (int v = 0; v < V2; ++v) F[m + 1][v] = u[m + H][v];
+          }
+          float contrib[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 ab = tab[DXS * r];
+            const float2 ta2 = make_float2(ab.x, ab.x), tb2 = make_float2(ab.y, ab.y);
+            [[maybe_unused]] float2 bse[V2];
+            if constexpr (STAGE == STAGE_HEUN2)
+              lds_vec2<T, V>(reinterpret_cast<const T*>(cur - H * C * (int)sizeof(T) + L::halo_bytes + r * PSTEP), bse);
+            float2 out[V2];
+            float2 pw2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int v = 0; v < V2; ++v) {
+              const float2 div = __ffma2_rn(ax2[v], sub2(F[r + 1][v], F[r][v]), __fmul2_rn(ay2[v], sub2(g[r][v], gprev[r][v])));
+              float2 t = sub2(__ffma2_rn(ta2, cm1[r][v], tb2), div);
+              if constexpr (STAGE == STAGE_HEUN2) t = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(bse[v], t));
+              t = make_float2(Store<T>::round(t.x), Store<T>::round(t.y));
+              out[v] = t;
+              pw2 = __ffma2_rn(w2[v], t, pw2);
+            }
+            contrib[r] = 0.f;
+            const int gx = x0 + s0 + DXS * r;
+            if (!XB || gx < nx) {
+              stg_vec2<T, V>(op + r * mstep, out);
+              contrib[r] = pw2.x + pw2.y;
+              if (XB || YB) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                  const float o = (v & 1) ? out[v / 2].y : out[v / 2].x;
+                  const float wv = (v & 1) ? w2[v / 2].y : w2[v / 2].x;
+                  const float xiv = d.xi[k0 + v], etav = d.eta[k0 + v];
+                  if (XB && gx == 0) bacc += ly_f * (wv * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
+                  if (XB && gx == nx - 1) bacc += ly_f * (wv * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
+                  if (YB && jrow == 0) bacc += lx_f * (wv * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
+                  if (YB && jrow == ny - 1) bacc += lx_f * (wv * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
+                }
+              }
+            }
+          }
+          float phys[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) phys[r] = (DXS > 0) ? contrib[r] : contrib[R - 1 - r];
+          const float sphi = multi_warp_sum<R>(phys, lane);
+          if ((lane & (32 / R - 1)) == 0) *tacc += sphi;
+          op += ostep;
+          tab += tstep;
+          tacc += tstep;
+          jrow += dys;
+        }
+        if (__syncthreads_or(!wok)) {   // a wait ran out somewhere: every warp stops here
+          ok = false;
+          break;
+        }
+        if (tid == 0 && q >= 1 && q - 1 + NS < total) {
+          fence_proxy_async_smem();
+          pull.issue(q - 1 + NS, nc, ni, pslot);
+        }
+        if (q >= 1 && ++ni == Lc) { ni = 0; ++nc; }
+        pslot = slot;
+        if (++slot == NS) { slot = 0; ph ^= 1u; }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int v = 0; v < V2; ++v) {
+            gprev[r][v] = g[r][v];
+            cm1[r][v] = c0[r][v];
+          }
+      }
+    };
+    if (d.cdir_x[c] > 0) chunk(std::integral_constant<int, 1>{});
+    else chunk(std::integral_constant<int, -1>{});
   }
   __syncthreads();
+  if (!ok) {
+    if (tid == 0) {
+      // drain: the last pull issued into each slot may still be in flight
+      for (int s = 0; s < NS; ++s) {
+        const int e = slot_pull[s];
+        if (e < 0 || (int64_t)e == d.drop_load) continue;
+        mbar_wait_bounded(&full[s], (uint32_t)((e / NS) & 1), limit);
+      }
+      atomicCAS(&st->status, DEV_OK, DEV_TIMEOUT);
+      st->timeout_where = ((int64_t)blockIdx.x << 32) | (int64_t)q;
+    }
+    return;
+  }
   cart_epilogue<TX, STAGE>(d, it, phi_out, tile_acc, red, x0, ya, nrows, bacc);
 }
 
 template <int ORDER, int R, int V, int STAGE, typename T, bool UNI>
-__global__ void __launch_bounds__(kCartThreads, 2)
+__global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
     cart_stage_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
   using L = CartCfg<ORDER, R, V, STAGE, T>;
   const WorkItem it = items[blockIdx.x];
@@ -782,22 +923,24 @@ static cudaError_t launch_one(const InstDesc* d_desc, const WorkItem* d_items, i
 }
 
 // Instantiation units: per storage type T and direction family U, the variants
-// order {1, 2} x run length 2 x ordinates per lane V (U = false: V = 1, 2, 4;
-// U = true: V = 2, 4) x stage.
-#define RTK_CART_STAGES(X, O, VV, U, TT) X(O, VV, STAGE_EULER, U, TT) X(O, VV, STAGE_HEUN1, U, TT) X(O, VV, STAGE_HEUN2, U, TT)
+// order {1, 2} x (run length R, ordinates per lane V) x stage, with (R, V) in
+// {(2, 1), (2, 2), (2, 4)} for U = false and {(2, 2), (2, 4), (4, 2)} for U = true.
+#define RTK_CART_STAGES(X, O, RR, VV, U, TT) \
+  X(O, RR, VV, STAGE_EULER, U, TT) X(O, RR, VV, STAGE_HEUN1, U, TT) X(O, RR, VV, STAGE_HEUN2, U, TT)
 #define RTK_CART_DEFINE_UNIT(NAME, TT, U, ...)                                                              \
-  cudaError_t cart_prepare_##NAME(int stage, int order, int vec, int ly_max) {                               \
+  cudaError_t cart_prepare_##NAME(int stage, int order, int run, int vec, int ly_max) {                      \
     RTK_CART_UNIT_LIST(RTK_CART_P_, TT, U)                                                                  \
     return cudaErrorInvalidValue;                                                                           \
   }                                                                                                         \
   cudaError_t cart_launch_##NAME(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,   \
-                                 int order, int vec, int ly_max, cudaStream_t stream) {                     \
+                                 int order, int run, int vec, int ly_max, cudaStream_t stream) {            \
     RTK_CART_UNIT_LIST(RTK_CART_L_, TT, U)                                                                  \
     return cudaErrorInvalidValue;                                                                           \
   }
-#define RTK_CART_P_(O, VV, ST, U, TT) \
-  if (order == O && vec == VV && stage == ST) return prepare_one<O, 2, VV, ST, TT, U>(ly_max);
-#define RTK_CART_L_(O, VV, ST, U, TT) \
-  if (order == O && vec == VV && stage == ST) return launch_one<O, 2, VV, ST, TT, U>(d_desc, d_items, n_items, ly_max, stream);
+#define RTK_CART_P_(O, RR, VV, ST, U, TT) \
+  if (order == O && run == RR && vec == VV && stage == ST) return prepare_one<O, RR, VV, ST, TT, U>(ly_max);
+#define RTK_CART_L_(O, RR, VV, ST, U, TT)                                  \
+  if (order == O && run == RR && vec == VV && stage == ST)                 \
+    return launch_one<O, RR, VV, ST, TT, U>(d_desc, d_items, n_items, ly_max, stream);
 
 }  // namespace rtk

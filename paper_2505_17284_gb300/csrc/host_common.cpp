@@ -296,20 +296,40 @@ static bool chunks_uniform(const rt_quadrature* quad, int Mpad, int V, int8_t* d
   return true;
 }
 
-static void choose_cart_tiles(Instance& I, int tile_x, int tile_y) {
-  (void)tile_x;   // one tile width (16 cells) in this build
-  I.run = 2;
+// Resident CTAs per SM of the Cartesian stage kernel at segment length ly: the
+// kernel's launch bound (2 with 8 values per thread and row, else 3) and its shared
+// memory (the Heun stage 2 ring is the largest).
+static int cart_ctas_per_sm(const Instance& I, int ly) {
+  const int by_regs = I.run * I.cvec >= 8 ? 2 : 3;
+  const int stage_hi = I.integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER;
+  const size_t smem = cart_smem_bytes(I.order, I.storage, I.run, I.cvec, ly, stage_hi) + 1024;
+  const int by_smem = (int)((size_t)228 * 1024 / smem);
+  return std::max(1, std::min(by_regs, by_smem));
+}
+
+static void choose_cart_tiles(Instance& I, int tile_y) {
   I.tx = cart_tile_width(I.run);
   I.n_strips = (I.nx + I.tx - 1) / I.tx;
-  const int sms = device_sm_count();
   int ly = tile_y;
   if (ly <= 0) {
-    // enough CTAs for a few per SM, with segments long enough that the 2H halo
-    // rows per segment stay a few percent of the rows read
-    const int target = 2 * sms;
-    const int segs = std::max(1, (target + I.n_strips - 1) / I.n_strips);
-    ly = (I.ny + segs - 1) / segs;
-    ly = std::max(8, std::min(ly, 64));
+    // Segment length by a wave model: a CTA pulls n_chunks * (ly + H + 1) rows
+    // per work item plus a fixed cost of about 4 rows (tile set-up, epilogue);
+    // the items run in waves of (resident CTAs per SM x SMs). Take the ly in
+    // [8, 64] with the least waves x rows per item (ties: the longer segment).
+    const int sms = device_sm_count();
+    const int chunks = std::max(1, I.Mpad / (32 * I.cvec));
+    double best = 0.0;
+    ly = 8;
+    for (int cand = 8; cand <= 64; ++cand) {
+      const int64_t items = (int64_t)I.n_strips * ((I.ny + cand - 1) / cand);
+      const int64_t slots = (int64_t)sms * cart_ctas_per_sm(I, cand);
+      const int64_t waves = (items + slots - 1) / slots;
+      const double cost = (double)waves * (chunks * (double)(std::min(cand, I.ny) + I.order + 1) + 4.0);
+      if (cand == 8 || cost <= best) {
+        best = cost;
+        ly = cand;
+      }
+    }
   }
   ly = std::max(1, std::min(ly, 256));
   I.ly = ly;
@@ -338,7 +358,7 @@ static void cell_range_items(int64_t n_cells, std::vector<WorkItem>& items) {
 rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
                          const rt_boundary* bc, int order, int integrator, int storage, double dt_target,
                          double t_end, int tile_x, int tile_y, DeviceArena& arena, cudaStream_t stream,
-                         Instance& I, std::vector<std::vector<char>>& keep, int variant) {
+                         Instance& I, std::vector<std::vector<char>>& keep, int variant, int vec) {
   if (!mesh) { set_error("mesh is NULL"); return RT_EINVAL; }
   int64_t n_cells = 0;
   if (mesh->kind == RT_MESH_CARTESIAN) {
@@ -402,23 +422,47 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     if (variant < 0 || variant > 2) { set_error("variant must be 0, 1 or 2"); return RT_EINVAL; }
     // per-lane width first; the chunk-uniform variant is taken (automatically) when
     // the same width also gives sign-uniform chunks, or when asked for
+    if (vec != 0 && vec != 1 && vec != 2 && vec != 4) { set_error("vec must be 0, 1, 2 or 4"); return RT_EINVAL; }
     I.uni = 0;
     I.cvec = choose_cart_vec(quad, I.Mpad);
-    if (variant != 1) {
-      for (int V = (variant == 2 ? 4 : I.cvec); V >= 2; V /= 2) {
+    if (vec != 0) {
+      if (vec > I.cvec) { set_error("vec %d: the quadrature allows at most %d ordinates per lane", vec, I.cvec); return RT_EINVAL; }
+      I.cvec = vec;
+    }
+    if (tile_x != 0 && tile_x != 16 && tile_x != 32) { set_error("tile_x must be 0, 16 or 32"); return RT_EINVAL; }
+    I.run = 2;
+    // 32-cell strips (runs of 4 cells per warp) with chunk-uniform directions and
+    // 2 ordinates per lane: fewer face evaluations and shared-memory reads per
+    // cell, but twice the chunks of 4 ordinates per lane. Chosen automatically
+    // only when 4 ordinates per lane do not give uniform chunks (the 16-cell
+    // strips with 4 per lane measured faster where both apply).
+    bool wide = false;
+    if (variant != 1 && (vec == 0 || vec == 2) && tile_x != 16) {
+      const bool narrow4 = tile_x == 0 && vec == 0 && I.cvec >= 4 && chunks_uniform(quad, I.Mpad, 4, cdx, cdy);
+      wide = !narrow4 && chunks_uniform(quad, I.Mpad, 2, cdx, cdy);
+    }
+    if (wide) {
+      I.uni = 1;
+      I.cvec = 2;
+      I.run = 4;
+    } else if (tile_x == 32) {
+      set_error("tile_x 32 needs chunk-uniform directions with 2 ordinates per lane");
+      return RT_EINVAL;
+    } else if (variant != 1) {
+      for (int V = (variant == 2 && vec == 0 ? 4 : I.cvec); V >= 2; V /= 2) {
         if (chunks_uniform(quad, I.Mpad, V, cdx, cdy)) {
           I.uni = 1;
           I.cvec = V;
           break;
         }
-        if (variant == 0) break;
+        if (variant == 0 || vec != 0) break;
       }
       if (variant == 2 && !I.uni) {
         set_error("variant 2 needs every ordinate chunk to have one sign of xi and one of eta");
         return RT_EINVAL;
       }
     }
-    choose_cart_tiles(I, tile_x, tile_y);
+    choose_cart_tiles(I, tile_y);
     I.stage_items.clear();
     const int n = I.n_strips * I.n_segs;
     for (int g = 0; g < I.n_segs; ++g)

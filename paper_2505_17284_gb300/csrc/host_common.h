@@ -69,7 +69,7 @@ struct Instance {
 rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
                          const rt_boundary* bc, int order, int integrator, int storage, double dt, double t_end,
                          int tile_x, int tile_y, DeviceArena& arena, cudaStream_t stream, Instance& inst,
-                         std::vector<std::vector<char>>& host_keepalive, int variant = 0);
+                         std::vector<std::vector<char>>& host_keepalive, int variant = 0, int vec = 0);
 
 int device_sm_count();
 

@@ -59,7 +59,8 @@ class rt_options(C.Structure):
     _fields_ = [("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("variant", C.c_int32),
                 ("dt", C.c_double), ("t_end", C.c_double),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p),
+                ("vec", C.c_int32), ("pad", C.c_int32)]
 
 
 class rt_qoi_t(C.Structure):
@@ -80,7 +81,8 @@ class rt_info_t(C.Structure):
 
 class rt_problem(C.Structure):
     _fields_ = [("mesh", rt_mesh), ("mat", rt_materials), ("quad", rt_quadrature), ("bc", rt_boundary),
-                ("order", C.c_int32), ("integrator", C.c_int32), ("dt", C.c_double), ("t_end", C.c_double)]
+                ("order", C.c_int32), ("integrator", C.c_int32), ("dt", C.c_double), ("t_end", C.c_double),
+                ("tile_y", C.c_int32), ("variant", C.c_int32), ("vec", C.c_int32), ("pad", C.c_int32)]
 
 
 RT_STAGE_EULER, RT_STAGE_HEUN1, RT_STAGE_HEUN2 = 0, 1, 2
@@ -117,7 +119,12 @@ SIGNATURES = {
     "rt_debug_set": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
     "rt_destroy": (None, [C.c_void_p]),
     "rt_last_error": (C.c_char_p, []),
-    "rt_batch_create": (C.c_int, [C.c_int32, C.POINTER(rt_problem), C.POINTER(rt_options), C.POINTER(C.c_void_p)]),
+    "rt_batch_create": (C.c_int, [C.c_int32, C.POINTER(rt_problem), C.c_int32, C.POINTER(rt_options),
+                                  C.POINTER(C.c_void_p)]),
+    "rt_batch_add": (C.c_int, [C.c_void_p, C.POINTER(rt_problem), C.POINTER(C.c_int32)]),
+    "rt_batch_remove": (C.c_int, [C.c_void_p, C.c_int32]),
+    "rt_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "rt_batch_progress": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "rt_batch_run": (C.c_int, [C.c_void_p, C.c_int64]),
     "rt_batch_qoi": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(rt_qoi_t)]),
     "rt_batch_get_psi": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64]),
@@ -328,10 +335,10 @@ class TorchAllocator:
 
 
 def make_options(order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=1.0, tile_x=0, tile_y=0,
-                 allocator: TorchAllocator | None = None, stream=None, variant=0) -> rt_options:
+                 allocator: TorchAllocator | None = None, stream=None, variant=0, vec=0) -> rt_options:
     o = rt_options()
     o.order, o.integrator, o.storage = order, integrator, storage
-    o.tile_x, o.tile_y, o.variant = tile_x, tile_y, variant
+    o.tile_x, o.tile_y, o.variant, o.vec = tile_x, tile_y, variant, vec
     o.dt, o.t_end = dt, t_end
     if allocator is not None:
         allocator.fill(o)
@@ -344,12 +351,12 @@ class Solver:
     """One problem on the GPU: create -> step -> qoi, through the C ABI."""
 
     def __init__(self, problem, quad, order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=None,
-                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0):
+                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0, vec=0):
         keep = _Keep()
         mesh, mat, q, bc = make_structs(problem, quad, keep)
         self.allocator = TorchAllocator() if use_torch_allocator else None
         opts = make_options(order, integrator, storage, dt, problem.t_end if t_end is None else t_end,
-                            tile_x, tile_y, self.allocator, variant=variant)
+                            tile_x, tile_y, self.allocator, variant=variant, vec=vec)
         self.h = rt_create(mesh, mat, q, bc, opts)
         self.info = rt_info(self.h)
         self.n_cells, self.M = int(self.info.n_cells), int(self.info.M)
@@ -387,28 +394,58 @@ class Solver:
             pass
 
 
-class Batch:
-    """Many problems advanced together (rt_batch_*)."""
+def make_problem(problem, quad, keep, order=2, integrator=RT_HEUN, dt=0.0, tile_y=0, variant=0, vec=0):
+    """rt_problem for a problem from sn_inputs and a quadrature (xi, eta, mu, w)."""
+    pr = rt_problem()
+    mesh, mat, q, bc = make_structs(problem, quad, keep)
+    pr.mesh, pr.mat, pr.quad, pr.bc = mesh, mat, q, bc
+    pr.order, pr.integrator, pr.dt, pr.t_end = order, integrator, float(dt), float(problem.t_end)
+    pr.tile_y, pr.variant, pr.vec = tile_y, variant, vec
+    return pr, (problem.mesh.n_cells, len(quad[0]), mat.n_regions)
 
-    def __init__(self, problems, quads, order=2, integrator=RT_HEUN, storage=RT_FP32, dts=None,
-                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0):
+
+class Batch:
+    """Many problems advanced together (rt_batch_*): a fixed number of slots,
+    problems added and removed between steps."""
+
+    def __init__(self, problems=(), quads=(), order=2, integrator=RT_HEUN, storage=RT_FP32, dts=None,
+                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0, vec=0, capacity=0, integrators=None,
+                 orders=None):
         keep = _Keep()
         k = len(problems)
-        arr = (rt_problem * k)()
-        self.shapes = []
+        arr = (rt_problem * max(k, 1))()
+        self.shapes = {}
         for i, (p, qd) in enumerate(zip(problems, quads)):
-            mesh, mat, q, bc = make_structs(p, qd, keep)
-            arr[i].mesh, arr[i].mat, arr[i].quad, arr[i].bc = mesh, mat, q, bc
-            arr[i].order = order if not isinstance(order, (list, tuple)) else order[i]
-            arr[i].integrator = integrator
-            arr[i].dt = 0.0 if dts is None else float(dts[i])
-            arr[i].t_end = p.t_end
-            self.shapes.append((p.mesh.n_cells, len(qd[0]), mat.n_regions))
+            o = order if orders is None else orders[i]
+            ig = integrator if integrators is None else integrators[i]
+            arr[i], self.shapes[i] = make_problem(p, qd, keep, o, ig, 0.0 if dts is None else dts[i])
         self.allocator = TorchAllocator() if use_torch_allocator else None
-        opts = make_options(storage=storage, tile_x=tile_x, tile_y=tile_y, allocator=self.allocator, variant=variant)
+        opts = make_options(storage=storage, tile_x=tile_x, tile_y=tile_y, allocator=self.allocator, variant=variant,
+                            vec=vec)
         self.h = C.c_void_p()
-        check(_fns().rt_batch_create(k, arr, C.byref(opts), C.byref(self.h)))
+        check(_fns().rt_batch_create(k, arr, capacity, C.byref(opts), C.byref(self.h)))
         self.k = k
+
+    def add(self, problem, quad, order=2, integrator=RT_HEUN, dt=0.0, tile_y=0, variant=0, vec=0) -> int:
+        keep = _Keep()
+        pr, shape = make_problem(problem, quad, keep, order, integrator, dt, tile_y, variant, vec)
+        slot = C.c_int32()
+        check(_fns().rt_batch_add(self.h, C.byref(pr), C.byref(slot)))
+        self.shapes[slot.value] = shape
+        return slot.value
+
+    def remove(self, slot: int):
+        check(_fns().rt_batch_remove(self.h, slot))
+        self.shapes.pop(slot, None)
+
+    def step(self, n: int):
+        check(_fns().rt_batch_step(self.h, int(n)))
+        return self
+
+    def progress(self, slot: int):
+        done, total = C.c_int64(), C.c_int64()
+        check(_fns().rt_batch_progress(self.h, slot, C.byref(done), C.byref(total)))
+        return done.value, total.value
 
     def run(self, max_steps=0):
         check(_fns().rt_batch_run(self.h, int(max_steps)))

@@ -115,16 +115,21 @@ def test_random_state_one_step_elementwise(rt, order, integrator):
     check_qoi(q, acc, S, 3, scale=S["mass"])
 
 
-@pytest.mark.parametrize("n_p,n_phi,variant", [(4, 16, 0), (8, 16, 0), (2, 16, 0), (8, 32, 1), (8, 32, 2),
-                                               (16, 32, 1), (16, 32, 2), (4, 64, 2)])
+@pytest.mark.parametrize("n_p,n_phi,variant,tile_x", [(4, 16, 0, 0), (8, 16, 0, 0), (2, 16, 0, 0), (8, 32, 1, 0),
+                                                      (8, 32, 2, 16), (8, 32, 0, 32), (16, 32, 1, 0), (16, 32, 2, 16),
+                                                      (16, 32, 2, 32), (4, 64, 2, 16), (4, 64, 0, 32)])
 @pytest.mark.parametrize("order", [1, 2])
-def test_kernel_variants(rt, n_p, n_phi, variant, order):
-    """Ordinates per lane (1, 2, 4) and both direction families (per-lane and
-    chunk-uniform) on a 91^2 grid (ragged tiles) from a smooth state, Heun."""
+def test_kernel_variants(rt, n_p, n_phi, variant, tile_x, order):
+    """Ordinates per lane (1, 2, 4), both direction families (per-lane and
+    chunk-uniform) and both strip widths (16 and 32 cells) on a 91^2 grid (ragged
+    tiles) from a smooth state, Heun."""
     p = si.lattice_problem(91)
     psi0 = si.smooth_psi(p.mesh, n_p * n_phi, seed=3)
     quad_lib = rt.rt_quad_product(n_p, n_phi)
-    s = rt.Solver(p, quad_lib, order=order, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, variant=variant)
+    s = rt.Solver(p, quad_lib, order=order, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, variant=variant,
+                  tile_x=tile_x)
+    if tile_x:
+        assert s.info.tile_x == tile_x
     s.set_psi(psi0)
     s.step(5)
     psi, q, dt = s.psi(), s.qoi(), s.info.dt
@@ -143,6 +148,15 @@ def test_uniform_variant_rejected_for_mixed_chunks(rt):
     with pytest.raises(rt.RTError) as e:
         rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.25, variant=2)
     assert e.value.code == rt.RT_EINVAL
+
+
+def test_wide_strips_need_uniform_pairs(rt):
+    p = si.lattice_problem(14)
+    with pytest.raises(rt.RTError) as e:
+        rt.Solver(p, rt.rt_quad_product(4, 16), order=2, integrator=rt.RT_HEUN, dt=0.25, tile_x=32)
+    assert e.value.code == rt.RT_EINVAL
+    with pytest.raises(rt.RTError):
+        rt.Solver(p, rt.rt_quad_product(16, 32), order=2, integrator=rt.RT_HEUN, dt=0.25, tile_x=24)
 
 
 def test_mixed_sign_quadrature_groups(rt):
@@ -375,4 +389,96 @@ def test_batch_against_oracle(rt):
         ref, acc, S = oracle.run(op, np.zeros((pr.mesh.n_cells, n_p * n_phi)), pr.t_end / n, n, "heun")
         assert rel_l2(b.psi(i), ref) <= PSI_TOL
         check_qoi(b.qoi(i), acc, S, 3, scale=S["mass"])
+    b.close()
+
+
+def _solo(rt, pr, qd, order, integrator, dt, n=None):
+    s = rt.Solver(pr, qd, order=order, integrator=integrator, dt=dt)
+    s.step(n)
+    out = (s.psi(), s.qoi())
+    s.close()
+    return out
+
+
+def test_batch_mixed_kinds_and_integrators_bitwise(rt):
+    """Cartesian MUSCL-Heun, Cartesian first-order Euler and a triangle mesh in
+    one batch: each result is bit-identical to its solve alone."""
+    a = si.lattice_problem(28, sigma_a_blue=9.0)
+    a.t_end = 0.9
+    c = si.enclosure_problem(12, seed=3, t_end=0.5)
+    e = si.lattice_problem(35, sigma_s_scatter=0.8)
+    e.t_end = 0.6
+    probs = [a, c, e]
+    quads = [rt.rt_quad_product(2, 16), rt.rt_quad_product(2, 8), rt.rt_quad_product(4, 16)]
+    orders = [2, 1, 1]
+    integ = [rt.RT_HEUN, rt.RT_EULER, rt.RT_EULER]
+    dts = [0.5 * a.mesh.dx, 0.0, 0.5 * e.mesh.dx]
+    b = rt.Batch(probs, quads, dts=dts, orders=orders, integrators=integ)
+    b.run()
+    for i in range(3):
+        ref_psi, ref_q = _solo(rt, probs[i], quads[i], orders[i], integ[i], dts[i])
+        assert np.array_equal(b.psi(i), ref_psi), i
+        q = b.qoi(i)
+        for k in q:
+            assert np.array_equal(np.asarray(q[k]), np.asarray(ref_q[k])), (i, k)
+    b.close()
+
+
+def test_batch_add_remove_between_steps(rt):
+    """Continuous batching: problems join and leave between steps; every
+    problem's result still equals its solve alone, and progress counts the
+    steps each one has taken."""
+    p0 = si.lattice_problem(21, sigma_a_blue=6.0)
+    p0.t_end = 2.0                      # 12 steps
+    p1 = si.lattice_problem(28, sigma_s_scatter=1.1)
+    p1.t_end = 2.0                      # 16 steps
+    p2 = si.enclosure_problem(10, seed=7, t_end=0.4)
+    q0, q1, q2 = rt.rt_quad_product(2, 8), rt.rt_quad_product(2, 16), rt.rt_quad_product(2, 8)
+    dt0, dt1 = 0.5 * p0.mesh.dx, 0.5 * p1.mesh.dx
+    b = rt.Batch([p0], [q0], dts=[dt0], capacity=3)
+    b.step(3)
+    s1 = b.add(p1, q1, order=2, integrator=rt.RT_HEUN, dt=dt1)
+    assert s1 == 1
+    b.step(5)
+    assert b.progress(0)[0] == 8 and b.progress(1)[0] == 5
+    psi0_after_8 = b.psi(0)
+    b.remove(0)
+    with pytest.raises(rt.RTError):
+        b.progress(0)
+    s2 = b.add(p2, q2, order=1, integrator=rt.RT_EULER)
+    assert s2 == 0                      # the freed slot is reused
+    b.step(4)
+    assert b.progress(1)[0] == 9 and b.progress(0)[0] == 4
+    b.run()
+    for slot, (pr, qd, o, ig, dt) in ((1, (p1, q1, 2, rt.RT_HEUN, dt1)), (0, (p2, q2, 1, rt.RT_EULER, 0.0))):
+        done, total = b.progress(slot)
+        assert done == total
+        ref_psi, ref_q = _solo(rt, pr, qd, o, ig, dt)
+        assert np.array_equal(b.psi(slot), ref_psi), slot
+        assert b.qoi(slot)["mass"] == ref_q["mass"]
+    # p0 left after 8 of its steps: its state then equals 8 steps alone
+    s = rt.Solver(p0, q0, order=2, integrator=rt.RT_HEUN, dt=dt0)
+    s.step(8)
+    assert np.array_equal(psi0_after_8, s.psi())
+    s.close()
+    b.close()
+
+
+def test_batch_capacity_and_empty_slots(rt):
+    p = si.lattice_problem(14)
+    p.t_end = 0.3
+    q = rt.rt_quad_product(2, 8)
+    b = rt.Batch([], [], capacity=1)
+    b.step(2)                           # nothing to do
+    slot = b.add(p, q, order=1, integrator=rt.RT_EULER)
+    with pytest.raises(rt.RTError) as e:
+        b.add(p, q, order=1, integrator=rt.RT_EULER)
+    assert e.value.code == rt.RT_EINVAL and "no free slot" in rt.rt_last_error()
+    with pytest.raises(rt.RTError):
+        b.qoi(slot + 1)
+    b.run()
+    done, total = b.progress(slot)
+    assert done == total > 0
+    b.step(3)                           # finished problems do not step further
+    assert b.progress(slot)[0] == total
     b.close()
