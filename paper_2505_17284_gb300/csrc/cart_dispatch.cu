@@ -9,10 +9,12 @@ namespace rtk {
   cudaError_t cart_launch_##NAME(const InstDesc*, const WorkItem*, int, int, int, int, int, int, \
                                  cudaStream_t);
 RTK_UNIT_DECL(f32_lane)
-RTK_UNIT_DECL(f32_uni)
+RTK_UNIT_DECL(f32_uni2v2)
+RTK_UNIT_DECL(f32_uni2v4)
 RTK_UNIT_DECL(f32_uni4)
 RTK_UNIT_DECL(bf16_lane)
-RTK_UNIT_DECL(bf16_uni)
+RTK_UNIT_DECL(bf16_uni2v2)
+RTK_UNIT_DECL(bf16_uni2v4)
 RTK_UNIT_DECL(bf16_uni4)
 #undef RTK_UNIT_DECL
 
@@ -33,11 +35,11 @@ cudaError_t prepare_cart_stage(int stage, int order, int storage, int run, int v
   if (storage == 0) {
     if (!uni) return cart_prepare_f32_lane(stage, order, run, vec, ly_max);
     return run == 4 ? cart_prepare_f32_uni4(stage, order, run, vec, ly_max)
-                    : cart_prepare_f32_uni(stage, order, run, vec, ly_max);
+                    : (vec == 4 ? cart_prepare_f32_uni2v4 : cart_prepare_f32_uni2v2)(stage, order, run, vec, ly_max);
   }
   if (!uni) return cart_prepare_bf16_lane(stage, order, run, vec, ly_max);
   return run == 4 ? cart_prepare_bf16_uni4(stage, order, run, vec, ly_max)
-                  : cart_prepare_bf16_uni(stage, order, run, vec, ly_max);
+                  : (vec == 4 ? cart_prepare_bf16_uni2v4 : cart_prepare_bf16_uni2v2)(stage, order, run, vec, ly_max);
 }
 
 cudaError_t launch_cart_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage, int order,
@@ -47,11 +49,11 @@ cudaError_t launch_cart_stage(const InstDesc* d_desc, const WorkItem* d_items, i
   if (storage == 0) {
     if (!uni) return cart_launch_f32_lane(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream);
     return run == 4 ? cart_launch_f32_uni4(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream)
-                    : cart_launch_f32_uni(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream);
+                    : (vec == 4 ? cart_launch_f32_uni2v4 : cart_launch_f32_uni2v2)(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream);
   }
   if (!uni) return cart_launch_bf16_lane(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream);
   return run == 4 ? cart_launch_bf16_uni4(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream)
-                  : cart_launch_bf16_uni(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream);
+                  : (vec == 4 ? cart_launch_bf16_uni2v4 : cart_launch_bf16_uni2v2)(d_desc, d_items, n_items, stage, order, run, vec, ly_max, stream);
 }
 
 template <typename T>

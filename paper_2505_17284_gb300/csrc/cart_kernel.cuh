@@ -573,9 +573,17 @@ struct UniPull {
 // sm_103a than this one barrier per row.) The waits are bounded; the barrier
 // also carries a failed wait, so all warps stop together, drain the loads in
 // flight and report the timeout.
-template <int ORDER, int R, int V, int STAGE, typename T, bool XB>
+// Register window of one row of the chunk-uniform tile, per lane: the row's
+// values c, their difference to the row before along the flow d, and the face
+// value g between the row before and this row.
+template <int R, int V2>
+struct UniRow {
+  float2 c[R][V2], d[R][V2], g[R][V2];
+};
+
+template <int ORDER, int R, int V, int STAGE, typename T, bool XB, bool YB>
 __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem& it, InstState* st,
-                                              uint8_t* smem, const bool YB) {
+                                              uint8_t* smem) {
   using L = CartCfg<ORDER, R, V, STAGE, T>;
   constexpr int H = L::H, TX = L::TX, C = L::C, NS = L::NS, NL = L::NL;
   constexpr int V2 = V / 2;   // ordinate pairs per lane: arithmetic runs on float pairs
@@ -684,34 +692,30 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
       const int tstep = dys * TX;
       float* tacc = tile_acc + (start - ya) * TX + xl0 + lane / (32 / R);
       int jrow = start;    // row completed next
-
-      float2 cm1[R][V2], dprev[R][V2], rprev[R][V2], gprev[R][V2];
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int v = 0; v < V2; ++v) cm1[r][v] = dprev[r][v] = rprev[r][v] = gprev[r][v] = make_float2(0.f, 0.f);
-
       int p = start - dys * H;
-      for (int i = 0; i < Lc; ++i, ++q, p += dys) {
+
+      // Row i of the chunk (row p of the grid) into window X; Y holds the row
+      // before it, which is completed here. The two windows swap roles from row
+      // to row, so no register is copied.
+      auto row = [&](const int i, UniRow<R, V2>& X, const UniRow<R, V2>& Y) -> bool {
         const bool wok = mbar_wait_bounded(&full[slot], ph, limit);
         const uint8_t* cur = ring + slot * L::slot_bytes + lofs;
-        float2 c0[R][V2];
-        const bool p_in = (p >= 0 && p < ny);
+        bool p_in = true;
+        if constexpr (YB) p_in = (p >= 0 && p < ny);
         if (YB && !p_in) {
           const float gv = (i < H) ? gy_up : 0.f;   // after the tile only the first-order face sees it
 #pragma unroll
           for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int v = 0; v < V2; ++v) c0[r][v] = make_float2(gv, gv);
+            for (int v = 0; v < V2; ++v) X.c[r][v] = make_float2(gv, gv);
         } else {
 #pragma unroll
-          for (int r = 0; r < R; ++r) lds_vec2<T, V>(reinterpret_cast<const T*>(cur + r * PSTEP), c0[r]);
+          for (int r = 0; r < R; ++r) lds_vec2<T, V>(reinterpret_cast<const T*>(cur + r * PSTEP), X.c[r]);
         }
         // face between the previous row (upwind) and row p
-        float2 g[R][V2];
         if constexpr (ORDER == 2) {
           bool second = true;
-          if (YB) {
+          if constexpr (YB) {
             const int pp = p - dys;
             if ((pp >= 0 && pp < ny) != p_in) second = false;   // domain boundary face: first order
           }
@@ -719,19 +723,16 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
           for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int v = 0; v < V2; ++v) {
-              const float2 dn = sub2(c0[r][v], cm1[r][v]);
-              const float2 rn = relu2(dn);
-              g[r][v] = second ? __ffma2_rn(make_float2(0.5f, 0.5f), minmod2r(dn, dprev[r][v], rn, rprev[r][v]),
-                                            cm1[r][v])
-                               : cm1[r][v];
-              dprev[r][v] = dn;
-              rprev[r][v] = rn;
+              X.d[r][v] = sub2(X.c[r][v], Y.c[r][v]);
+              const float2 ext = __ffma2_rn(make_float2(0.5f, 0.5f),
+                                            minmod2r(X.d[r][v], Y.d[r][v], relu2(X.d[r][v]), relu2(Y.d[r][v])), Y.c[r][v]);
+              X.g[r][v] = (!YB || second) ? ext : Y.c[r][v];
             }
         } else {
 #pragma unroll
           for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int v = 0; v < V2; ++v) g[r][v] = cm1[r][v];
+            for (int v = 0; v < V2; ++v) X.g[r][v] = Y.c[r][v];
         }
         // completion of the previous row (its slot, pull q - 1, is still resident)
         if (i >= H + 1) {
@@ -743,14 +744,12 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
             if constexpr (XB) {
               const int gpos = x0 + s0 + DXS * (m - H);
               if (gpos < 0 || gpos >= nx) {
+                // entering ordinates see psi^- of the side, leaving ones nothing (only
+                // first-order faces read it)
+                const float gside = (gpos < 0) ? d.ghost[0] : d.ghost[1];
+                const bool enter = (gpos < 0) == (DXS > 0);
 #pragma unroll
-                for (int v = 0; v < V2; ++v) {
-                  // entering ordinates see psi^- of the side, leaving ones nothing (only
-                  // first-order faces read it)
-                  const float gside = (gpos < 0) ? d.ghost[0] : d.ghost[1];
-                  const bool enter = (gpos < 0) == (DXS > 0);
-                  u[m][v] = enter ? make_float2(gside, gside) : make_float2(0.f, 0.f);
-                }
+                for (int v = 0; v < V2; ++v) u[m][v] = enter ? make_float2(gside, gside) : make_float2(0.f, 0.f);
               }
             }
           }
@@ -797,8 +796,8 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
             float2 pw2 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int v = 0; v < V2; ++v) {
-              const float2 div = __ffma2_rn(ax2[v], sub2(F[r + 1][v], F[r][v]), __fmul2_rn(ay2[v], sub2(g[r][v], gprev[r][v])));
-              float2 t = sub2(__ffma2_rn(ta2, cm1[r][v], tb2), div);
+              const float2 div = __ffma2_rn(ax2[v], sub2(F[r + 1][v], F[r][v]), __fmul2_rn(ay2[v], sub2(X.g[r][v], Y.g[r][v])));
+              float2 t = sub2(__ffma2_rn(ta2, Y.c[r][v], tb2), div);
               if constexpr (STAGE == STAGE_HEUN2) t = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(bse[v], t));
               t = make_float2(Store<T>::round(t.x), Store<T>::round(t.y));
               out[v] = t;
@@ -833,10 +832,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
           tacc += tstep;
           jrow += dys;
         }
-        if (__syncthreads_or(!wok)) {   // a wait ran out somewhere: every warp stops here
-          ok = false;
-          break;
-        }
+        if (__syncthreads_or(!wok)) return false;   // a wait ran out somewhere: every warp stops here
         if (tid == 0 && q >= 1 && q - 1 + NS < total) {
           fence_proxy_async_smem();
           pull.issue(q - 1 + NS, nc, ni, pslot);
@@ -844,13 +840,19 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
         if (q >= 1 && ++ni == Lc) { ni = 0; ++nc; }
         pslot = slot;
         if (++slot == NS) { slot = 0; ph ^= 1u; }
+        ++q;
+        p += dys;
+        return true;
+      };
+
+      UniRow<R, V2> A, B;
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-          for (int v = 0; v < V2; ++v) {
-            gprev[r][v] = g[r][v];
-            cm1[r][v] = c0[r][v];
-          }
+        for (int v = 0; v < V2; ++v) B.c[r][v] = B.d[r][v] = B.g[r][v] = make_float2(0.f, 0.f);
+      for (int i = 0; i < Lc; i += 2) {
+        if (!row(i, A, B)) { ok = false; break; }
+        if (i + 1 < Lc && !row(i + 1, B, A)) { ok = false; break; }
       }
     };
     if (d.cdir_x[c] > 0) chunk(std::integral_constant<int, 1>{});
@@ -890,8 +892,13 @@ __global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
   const bool xb = (x0 - L::H < 0) || (x0 + L::TX + L::H > d.nx);
   const bool yb = (ya - L::H < 0) || (ya + d.ly + L::H > d.ny);
   if constexpr (UNI) {
-    if (xb) cart_tile_uni<ORDER, R, V, STAGE, T, true>(d, it, st, smem, yb);
-    else cart_tile_uni<ORDER, R, V, STAGE, T, false>(d, it, st, smem, yb);
+    if (xb) {
+      if (yb) cart_tile_uni<ORDER, R, V, STAGE, T, true, true>(d, it, st, smem);
+      else cart_tile_uni<ORDER, R, V, STAGE, T, true, false>(d, it, st, smem);
+    } else {
+      if (yb) cart_tile_uni<ORDER, R, V, STAGE, T, false, true>(d, it, st, smem);
+      else cart_tile_uni<ORDER, R, V, STAGE, T, false, false>(d, it, st, smem);
+    }
   } else {
     if (xb) cart_tile<ORDER, R, V, STAGE, T, true>(d, it, st, smem, yb);
     else cart_tile<ORDER, R, V, STAGE, T, false>(d, it, st, smem, yb);

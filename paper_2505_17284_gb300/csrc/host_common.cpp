@@ -312,10 +312,12 @@ static void choose_cart_tiles(Instance& I, int tile_y) {
   I.n_strips = (I.nx + I.tx - 1) / I.tx;
   int ly = tile_y;
   if (ly <= 0) {
-    // Segment length by a wave model: a CTA pulls n_chunks * (ly + H + 1) rows
-    // per work item plus a fixed cost of about 4 rows (tile set-up, epilogue);
-    // the items run in waves of (resident CTAs per SM x SMs). Take the ly in
-    // [8, 64] with the least waves x rows per item (ties: the longer segment).
+    // Segment length by a throughput model: a CTA pulls n_chunks * (ly + H + 1)
+    // rows per work item plus a fixed cost of about 4 rows (tile set-up,
+    // epilogue); the block scheduler keeps (resident CTAs per SM x SMs) items in
+    // flight, and the last item of a slot adds about one item time. Take the ly
+    // in [8, 64] with the least items x item time / slots + item time (ties: the
+    // longer segment).
     const int sms = device_sm_count();
     const int chunks = std::max(1, I.Mpad / (32 * I.cvec));
     double best = 0.0;
@@ -323,8 +325,8 @@ static void choose_cart_tiles(Instance& I, int tile_y) {
     for (int cand = 8; cand <= 64; ++cand) {
       const int64_t items = (int64_t)I.n_strips * ((I.ny + cand - 1) / cand);
       const int64_t slots = (int64_t)sms * cart_ctas_per_sm(I, cand);
-      const int64_t waves = (items + slots - 1) / slots;
-      const double cost = (double)waves * (chunks * (double)(std::min(cand, I.ny) + I.order + 1) + 4.0);
+      const double t_item = chunks * (double)(std::min(cand, I.ny) + I.order + 1) + 4.0;
+      const double cost = (double)items * t_item / (double)std::min(items, slots) + t_item;
       if (cand == 8 || cost <= best) {
         best = cost;
         ly = cand;
