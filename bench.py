@@ -51,6 +51,36 @@ def bytes_per_update(order, integrator, storage):
     return (2 if integrator == "euler" else 5) * es
 
 
+KERNEL_SOURCES = {"cart": ["cart_kernel.cuh", "device_common.cuh"], "tri": ["tri_kernel.cu", "device_common.cuh"]}
+
+
+def kernel_sha(kind):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2505_17284_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, kind):
+    """DRAM bytes per cell-ordinate per step of the stage kernel, from the
+    'traffic:' line of a committed ncu summary under profiles/ for this
+    workload, or None when there is none or the kernel sources changed since
+    the capture (the summary records their hash)."""
+    import glob
+    sha = kernel_sha(kind)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                if not line.startswith("traffic:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if kv.get("workload") == workload and kv.get("kernel") == kind and kv.get("sha") == sha:
+                    return float(kv["bytes_per_update"]), os.path.relpath(path, ROOT)
+    return None, None
+
+
 def make_problem(spec):
     import sn_inputs as si
     mesh, n, n_p, n_phi, order, integ, storage, dtf, t_end = spec
@@ -247,6 +277,8 @@ def run_ours(args, spec):
         h2d = n_cells * (16 + 32) + 3 * info.M_pad * 4
     d2h = 336
 
+    tb, traffic_src = profiled_traffic(args.workload, "cart" if mesh == "lattice" else "tri")
+    traffic = tb * dof if tb is not None else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -259,9 +291,12 @@ def run_ours(args, spec):
                    "l2": f"inputs larger than L2 (psi {dof * (2 if storage == 'bf16' else 4) / 1e9:.2f} GB per buffer)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": achieved_gbs / peak, "traffic": None,
+                     "frac": achieved_gbs / peak, "traffic": traffic,
+                     "traffic_per": "step (all stage launches), DRAM read + write bytes",
+                     "traffic_source": traffic_src,
                      "kernel": "cart_stage_kernel" if mesh == "lattice" else "tri_stage_kernel",
-                     "bytes_per_update": bpu, "peak_source": f"{peak_src} hbm_gbs"},
+                     "bytes_per_update": bpu, "peak_source": f"{peak_src} hbm_gbs",
+                     "achieved_basis": "algorithmic bytes per cell-ordinate x cell-ordinates x steps / event time of the steps"},
         "e2e": {"value": dof * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                 "seconds": e2e_s, "includes": "rt_create from host arrays + K steps + rt_qoi read-back + rt_destroy"},
         "gpu_launches": K * launches_per_step,
