@@ -358,13 +358,192 @@ def run_reference(args, spec):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ sweeps and serving
+EXTRA_WORKLOADS = {
+    # lattice DP-1 sweep: 256 instances, grids {70,140,280,560}^2, M in {64,128,256}, MUSCL Heun FP32
+    "sweep256": dict(kind="sweep", k=256, grids=(70, 140, 280, 560)),
+    # the same draws restricted to small grids, where one solve cannot fill the GPU
+    "sweep256_small": dict(kind="sweep", k=256, grids=(70, 140)),
+    # Poisson stream of 200 mixed lattice / enclosure requests, end times x 0.1
+    "serve200": dict(kind="serve", count=200, horizon=0.1),
+}
+
+
+def _quads(rt, cache, n_p, n_phi):
+    key = (n_p, n_phi)
+    if key not in cache:
+        cache[key] = rt.rt_quad_product(n_p, n_phi)
+    return cache[key]
+
+
+def sweep_jobs(rt, k, grids, seed=0):
+    import sn_inputs as si
+    from paper_2505_17284_gb300.sweep import Job
+    qc, jobs = {}, []
+    for inst in si.sweep_instances(k, seed, grids=grids):
+        p = si.lattice_problem(inst.n, sigma_a_blue=inst.sigma_a, sigma_s_scatter=inst.sigma_s)
+        jobs.append(Job(p, _quads(rt, qc, inst.n_p, inst.n_phi), 2, rt.RT_HEUN, 0.5 * p.mesh.dx))
+    return jobs
+
+
+def _peak():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+    except Exception:
+        pk = None
+    return (pk, "measured hbm_gbs") if pk else (6800.0, "fallback hbm_gbs")
+
+
+def run_sweep(args, w):
+    import torch
+    from paper_2505_17284_gb300 import build as B, rt, autotune
+    from paper_2505_17284_gb300 import sweep as S
+    B.build()
+    rt.load_library()
+    jobs = sweep_jobs(rt, w["k"], w["grids"])
+    # autotuned tiles: one rt_autotune per distinct shape for the one-at-a-time
+    # path, and the batch-level segment length for the batched path
+    shapes = {}
+    for j in jobs:
+        shapes.setdefault((j.problem.mesh.nx, j.M), j)
+    for j in shapes.values():
+        autotune.tuned_config(j.problem, j.quad, j.order, j.integrator, rt.RT_FP32, j.dt, steps=3)
+    best_ty, ty_times = S.tune_batch(jobs, candidates=(0, 24, 48), steps=3)
+    clocks = ClockSampler(0)
+    clocks.start()
+    phases = {}
+    qb, tb, steps_b = S.solve_batched(jobs, tile_y=best_ty, phases=phases)
+    qp, tp, per, steps_p = S.solve_plain(jobs, tune=True)
+    clk = clocks.stop()
+    diff = max(S.qoi_rel_diff(a, b) for a, b in zip(qb, qp))
+    peak, peak_src = _peak()
+    nbytes = S.state_bytes(jobs, steps_b)
+    ideal = nbytes / (peak * 1e9)
+    updates = sum(float(j.n_cells) * j.M * n for j, n in zip(jobs, steps_b))
+    k = len(jobs)
+    out = {
+        "metric": "batched solves/s", "value": k / tb, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded lattice DP-1 sweep)",
+        "config": {"workload": args.workload, "instances": k, "grids": list(w["grids"]), "ordinates": [64, 128, 256],
+                   "sigma_a": "U[5,15]", "sigma_s": "U[0.5,1.5]", "scheme": "MUSCL Heun", "psi_storage": "fp32",
+                   "step": "one whole sweep (all instances to their N_t = 0.914 n)",
+                   "batch_tile_y": best_ty, "batch_tile_y_ms_per_step": ty_times,
+                   "plain_tiles": "rt_autotune per shape", "l2": "working set of the large-grid instances > L2"},
+        "plain": {"solves_per_s": k / tp, "seconds": tp, "path": "rt_create + rt_step(N_t) + rt_qoi + rt_destroy per instance"},
+        "batched_seconds": tb,
+        "batched_phases_s": phases,
+        "speedup_vs_plain": tp / tb,
+        "amdahl_bound": tp / ideal,
+        "amdahl_basis": "plain seconds / seconds of the sweep's algorithmic state bytes at the HBM peak",
+        "qoi_max_rel_diff_batched_vs_plain": diff,
+        "updates_per_s_batched": updates / tb,
+        "roofline": {"bound": "hbm", "achieved": nbytes / tb / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": nbytes / tb / 1e9 / peak, "traffic": None, "kernel": "cart_stage_kernel (batched)",
+                     "peak_source": peak_src},
+        "e2e": {"value": k / tb, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": k * 336,
+                "includes": "batch creation from host arrays, all steps, QoI read-back, destroy"},
+        "gpu_launches": {"batched": 2 * max(steps_b) * len({j.M for j in jobs}) + k,
+                         "plain": sum(2 * n + 1 for n in steps_p),
+                         "basis": "batched: 2 stage launches per step per kernel-variant group (one per ordinate "
+                                  "count) + one init per instance; plain: 2 per step + 1 init per instance"},
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
+def serve_requests(rt, count, horizon, storage, seed=0, arrivals=None):
+    import numpy as np
+    import sn_inputs as si
+    from paper_2505_17284_gb300.serve import Request, estimate_bytes
+    from paper_2505_17284_gb300.sweep import Job
+    specs = si.serve_requests(count, seed, horizon)
+    qc = {}
+    reqs = []
+    for i, sp in enumerate(specs):
+        q = _quads(rt, qc, sp.n_p, sp.n_phi)
+        if sp.kind == "lattice":
+            make = (lambda sp=sp, q=q: Job(si.lattice_problem(sp.n, t_end=sp.t_end), q, 2, rt.RT_HEUN, 0.5 * 7.0 / sp.n))
+            nb = estimate_bytes(sp.n * sp.n, sp.M, storage)
+        else:
+            make = (lambda sp=sp, q=q, i=i: Job(si.enclosure_problem(sp.n, jitter=0.2, seed=i, t_end=sp.t_end), q, 1,
+                                                rt.RT_EULER, 0.0))
+            nb = estimate_bytes(2 * sp.n * sp.n, sp.M, storage, triangles=True)
+        reqs.append(Request(rid=i, arrival=0.0 if arrivals is None else float(arrivals[i]), make=make, est_bytes=nb))
+    return reqs, specs
+
+
+def run_serve(args, w):
+    import numpy as np
+    import sn_inputs as si
+    from paper_2505_17284_gb300 import build as B, rt
+    from paper_2505_17284_gb300 import serve as SV
+    from paper_2505_17284_gb300.sweep import qoi_rel_diff
+    B.build()
+    rt.load_library()
+    count, horizon = w["count"], w["horizon"]
+    # capacity: the whole stream present at the start (closed loop), FP32
+    reqs, specs = serve_requests(rt, count, horizon, rt.RT_FP32)
+    t0 = time.perf_counter()
+    closed = SV.Server(storage=rt.RT_FP32).run(reqs, realtime=False)
+    cap = count / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+    arr = si.poisson_arrivals(count, rate, seed=0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = {}
+    for name, stor in (("fp32", rt.RT_FP32), ("bf16", rt.RT_BF16)):
+        reqs, _ = serve_requests(rt, count, horizon, stor, arrivals=arr)
+        t0 = time.perf_counter()
+        served = SV.Server(storage=stor).run(reqs, realtime=True)
+        span = max(s.finished for s in served)
+        res[name] = {"served": served, "span": span}
+    clk = clocks.stop()
+    reqs, _ = serve_requests(rt, count, horizon, rt.RT_FP32, arrivals=arr)
+    service, plain_q = SV.plain_service_times(reqs, rt.RT_FP32)
+    lat_plain, end_plain = SV.fifo_latencies(reqs, service)
+    q32 = {s.rid: s.qoi for s in res["fp32"]["served"]}
+    q16 = {s.rid: s.qoi for s in res["bf16"]["served"]}
+    d_bf16 = [qoi_rel_diff(q16[i], q32[i]) for i in range(count)]
+    d_plain = [qoi_rel_diff(q32[i], plain_q[i]) for i in range(count)]
+    out32 = res["fp32"]
+    lat32 = [s.latency for s in out32["served"]]
+    lat16 = [s.latency for s in res["bf16"]["served"]]
+    out = {
+        "metric": "served solves/s", "value": count / out32["span"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": out32["span"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded request stream)",
+        "config": {"workload": args.workload, "requests": count, "arrivals": f"Poisson, seed 0, rate {rate:.2f}/s "
+                   f"= 0.8 x closed-loop batched capacity {cap:.2f}/s",
+                   "mix": "50/50 lattice (n 70..700 step 70, MUSCL Heun) / enclosure triangles (n 130..650 step "
+                          "130, first order Euler), M in {64,128,256,512}",
+                   "end_times": f"lattice {3.2 * horizon:g}, enclosure {2.6 * horizon:g} (x{horizon:g} of the benchmarks')",
+                   "admission": "free slot (64) and device memory within 85% of free HBM at start",
+                   "chunk_steps": 16, "step": "the whole stream"},
+        "latency_s": {"fp32": SV.percentiles(lat32), "bf16": SV.percentiles(lat16),
+                      "plain_fifo_fp32": SV.percentiles(lat_plain.values())},
+        "solves_per_s": {"fp32": count / out32["span"], "bf16": count / res["bf16"]["span"],
+                         "plain_fifo_fp32": count / end_plain if end_plain > 0 else None,
+                         "plain_closed_loop_fp32": count / sum(service.values())},
+        "p99_vs_plain": SV.percentiles(lat_plain.values())["p99"] / SV.percentiles(lat32)["p99"],
+        "qoi_rel_diff": {"bf16_vs_fp32_max": max(d_bf16), "bf16_vs_fp32_median": float(np.median(d_bf16)),
+                         "served_fp32_vs_alone_max": max(d_plain)},
+        "e2e": {"value": count / out32["span"], "unit": "solves/s", "h2d_bytes_per_step": None,
+                "d2h_bytes_per_step": count * 336, "includes": "problem build on the host, admission, all steps, "
+                                                               "QoI read-back, removal"},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(EXTRA_WORKLOADS))
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -372,6 +551,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.workload in EXTRA_WORKLOADS:
+        w = EXTRA_WORKLOADS[args.workload]
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle is timed on single solves "
+                              "(the default workload); sweeps and streams are GPU-only reports"}))
+            return
+        (run_sweep if w["kind"] == "sweep" else run_serve)(args, w)
+        return
     spec = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, spec)

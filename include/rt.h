@@ -181,6 +181,8 @@ typedef struct {
   int32_t kind, order, integrator, storage;
   int32_t tile_x, tile_y, n_work_items, stages_per_step;
   int64_t device_bytes;
+  int32_t variant;   /* Cartesian kernel variant in use: 1 per-lane, 2 chunk-uniform (0: triangles) */
+  int32_t vec;       /* ordinates per lane */
 } rt_info_t;
 
 typedef struct rt_solver rt_solver;
@@ -247,6 +249,25 @@ void rt_destroy(rt_solver* s);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* rt_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner (Cartesian meshes). The paper has no counterpart: it chooses among
+ * the library's own kernel configurations. For the problem and options given,
+ * each candidate (strip width 16 or 32 cells, segment length in {auto, 16, 24,
+ * ..., 64} rows, per-lane or chunk-uniform directions; only those the
+ * quadrature and shared memory allow, and opts->variant/vec if set) is built
+ * as a full solver with rt_create, advanced one step, then timed with CUDA
+ * events over `steps` further steps (at most N_t - 1) on opts->stream, and
+ * destroyed. *best receives opts with tile_x, tile_y, variant and vec of the
+ * fastest candidate (so rt_create(..., best, ...) builds it), and
+ * *best_ms_per_step (may be NULL) its time per step. Device memory: one
+ * candidate's state at a time, allocated as rt_create does. When N_t < 2 the
+ * library's own choice is returned with time 0. RT_EINVAL for triangle meshes,
+ * steps outside 1..1000 or an invalid problem; errors of rt_create, rt_step or
+ * a device-side failure of a candidate are returned as they are. Synchronises
+ * opts->stream. */
+rt_status rt_autotune(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad, const rt_boundary* bc,
+                      const rt_options* opts, int32_t steps, rt_options* best, double* best_ms_per_step);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent problems advanced together by shared launches.

@@ -198,6 +198,8 @@ rt_status rt_info(const rt_solver* s, rt_info_t* out) {
   out->n_work_items = (int32_t)I.stage_items.size();
   out->stages_per_step = I.integrator == RT_HEUN ? 2 : 1;
   out->device_bytes = s->arena.bytes;
+  out->variant = I.kind == RT_MESH_CARTESIAN ? (I.uni ? 2 : 1) : 0;
+  out->vec = I.kind == RT_MESH_CARTESIAN ? I.cvec : I.vec;
   return RT_OK;
 }
 

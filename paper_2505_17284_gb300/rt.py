@@ -76,7 +76,8 @@ class rt_info_t(C.Structure):
                 ("dt", C.c_double), ("t_end", C.c_double),
                 ("kind", C.c_int32), ("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("n_work_items", C.c_int32),
-                ("stages_per_step", C.c_int32), ("device_bytes", C.c_int64)]
+                ("stages_per_step", C.c_int32), ("device_bytes", C.c_int64), ("variant", C.c_int32),
+                ("vec", C.c_int32)]
 
 
 class rt_problem(C.Structure):
@@ -130,6 +131,9 @@ SIGNATURES = {
     "rt_batch_get_psi": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64]),
     "rt_batch_destroy": (None, [C.c_void_p]),
     "rt_cart_stage_noalloc": (C.c_int, [C.POINTER(rt_cart_stage_args)]),
+    "rt_autotune": (C.c_int, [C.POINTER(rt_mesh), C.POINTER(rt_materials), C.POINTER(rt_quadrature),
+                              C.POINTER(rt_boundary), C.POINTER(rt_options), C.c_int32, C.POINTER(rt_options),
+                              C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -347,11 +351,34 @@ def make_options(order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=1.
     return o
 
 
+def rt_autotune(problem, quad, order=2, integrator=RT_HEUN, storage=RT_FP32, dt=0.0, t_end=None, steps=4,
+                variant=0, vec=0):
+    """Time the candidate Cartesian configurations of this problem on the
+    current device (rt_autotune); returns ({tile_x, tile_y, variant, vec},
+    ms per step of the fastest)."""
+    keep = _Keep()
+    mesh, mat, q, bc = make_structs(problem, quad, keep)
+    alloc = TorchAllocator()
+    opts = make_options(order, integrator, storage, dt, problem.t_end if t_end is None else t_end, 0, 0, alloc,
+                        variant=variant, vec=vec)
+    best = rt_options()
+    ms = C.c_double()
+    check(_fns().rt_autotune(C.byref(mesh), C.byref(mat), C.byref(q), C.byref(bc), C.byref(opts), int(steps),
+                             C.byref(best), C.byref(ms)))
+    return {"tile_x": best.tile_x, "tile_y": best.tile_y, "variant": best.variant, "vec": best.vec}, ms.value
+
+
 class Solver:
-    """One problem on the GPU: create -> step -> qoi, through the C ABI."""
+    """One problem on the GPU: create -> step -> qoi, through the C ABI.
+    tune=True takes the kernel configuration from the autotuner (cached per
+    device and problem shape; see autotune.py) instead of tile_x/tile_y/variant/vec."""
 
     def __init__(self, problem, quad, order=1, integrator=RT_EULER, storage=RT_FP32, dt=0.0, t_end=None,
-                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0, vec=0):
+                 tile_x=0, tile_y=0, use_torch_allocator=True, variant=0, vec=0, tune=False):
+        if tune and hasattr(problem.mesh, "nx"):
+            from . import autotune
+            cfg = autotune.tuned_config(problem, quad, order, integrator, storage, dt, t_end)
+            tile_x, tile_y, variant, vec = cfg["tile_x"], cfg["tile_y"], cfg["variant"], cfg["vec"]
         keep = _Keep()
         mesh, mat, q, bc = make_structs(problem, quad, keep)
         self.allocator = TorchAllocator() if use_torch_allocator else None

@@ -1,0 +1,162 @@
+"""Serving loop with continuous batching.
+
+Solve requests arrive over time. The server keeps one batch of slots on the
+GPU: an arrived request is admitted (its problem built, its state created and
+initialised on the device) as soon as a slot is free and its device memory
+fits in a budget taken from the free HBM at start; every admitted problem is
+advanced together with the others, in chunks of steps, by the same launches;
+a problem that reaches its own N_t is retired (QoIs read back, memory freed)
+and its slot and memory go to the next request. State stays on the device
+from admission to retirement. Latency is retirement time minus arrival time.
+
+The plain baseline serves the same stream first-in first-out with one solver
+at a time; its latencies follow from the measured service time of each
+request (a single FIFO server's latency does not depend on anything else).
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import Callable
+
+import numpy as np
+
+from . import rt
+from .sweep import Job
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the start of the stream
+    make: Callable[[], Job]        # builds the job (host work, counted in the latency)
+    est_bytes: int                 # device memory to reserve at admission
+
+
+@dataclass
+class Served:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    qoi: dict
+    slot: int = -1
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def estimate_bytes(n_cells: int, M: int, storage=rt.RT_FP32, triangles=False) -> int:
+    """Upper estimate of a problem's device memory: two psi buffers (ordinates
+    padded to 32), two phi buffers and per-cell metadata (larger for
+    triangles: neighbours, edge geometry, areas), plus fixed overhead."""
+    es = 2 if storage == rt.RT_BF16 else 4
+    Mpad = (M + 31) // 32 * 32
+    per_cell = 2 * Mpad * es + 16 + (96 if triangles else 8)
+    return int(n_cells * per_cell + (8 << 20))
+
+
+@dataclass
+class Server:
+    storage: int = rt.RT_FP32
+    capacity: int = 64             # slots
+    chunk: int = 16                # steps per enqueue
+    mem_fraction: float = 0.85     # of the free HBM at start
+    reserve: int = 2 << 30         # bytes kept free for the allocator's own use
+    max_ahead: int = 2             # chunks enqueued ahead of the device
+    log: list = field(default_factory=list)
+
+    def run(self, requests, realtime=True):
+        """Serve `requests` (arrival times relative to the start); with
+        realtime=False every request is present at the start (closed loop).
+        Returns the list of Served, in completion order."""
+        import torch
+        free, _ = torch.cuda.mem_get_info()
+        budget = int(free * self.mem_fraction) - self.reserve
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = collections.deque()
+        active = {}                     # slot -> (request, admitted time, bytes)
+        used = 0
+        events = collections.deque()
+        done = []
+        b = rt.Batch([], [], storage=self.storage, capacity=self.capacity)
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        try:
+            while pending or waiting or active:
+                t = now()
+                while pending and (not realtime or pending[0].arrival <= t):
+                    waiting.append(pending.popleft())
+                while waiting and len(active) < self.capacity and used + waiting[0].est_bytes <= budget:
+                    r = waiting.popleft()
+                    j = r.make()
+                    slot = b.add(j.problem, j.quad, order=j.order, integrator=j.integrator, dt=j.dt)
+                    active[slot] = (r, now(), r.est_bytes)
+                    used += r.est_bytes
+                if not active:
+                    if waiting:
+                        raise RuntimeError(f"request {waiting[0].rid} needs {waiting[0].est_bytes} bytes, "
+                                           f"more than the budget of {budget}")
+                    if pending:
+                        time.sleep(max(0.0, pending[0].arrival - now()))
+                    continue
+                b.step(self.chunk)
+                ev = torch.cuda.Event()
+                ev.record()
+                events.append(ev)
+                finished = []
+                for slot in active:
+                    d, n = b.progress(slot)
+                    if d >= n:
+                        finished.append(slot)
+                if finished:
+                    for slot in finished:
+                        q = b.qoi(slot)          # synchronises
+                        r, adm, nb = active.pop(slot)
+                        done.append(Served(r.rid, r.arrival, adm, now(), q, slot))
+                        b.remove(slot)
+                        used -= nb
+                    events.clear()
+                elif len(events) > self.max_ahead:
+                    events.popleft().synchronize()
+        finally:
+            b.close()
+        return done
+
+
+def plain_service_times(requests, storage=rt.RT_FP32, tune=False):
+    """Solve every request alone, one after another; returns ({rid: seconds},
+    {rid: QoIs}). Each time covers building the job, creating the solver,
+    stepping to N_t, reading the QoIs and destroying it."""
+    import torch
+    times, qois = {}, {}
+    for r in requests:
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        j = r.make()
+        s = rt.Solver(j.problem, j.quad, order=j.order, integrator=j.integrator, storage=storage, dt=j.dt, tune=tune)
+        s.step()
+        qois[r.rid] = s.qoi()
+        s.close()
+        torch.cuda.synchronize()
+        times[r.rid] = time.perf_counter() - a
+    return times, qois
+
+
+def fifo_latencies(requests, service):
+    """Latencies of a single first-in first-out server with the given service
+    times, for the requests' arrival times."""
+    end = 0.0
+    lat = {}
+    for r in sorted(requests, key=lambda r: r.arrival):
+        start = max(r.arrival, end)
+        end = start + service[r.rid]
+        lat[r.rid] = end - r.arrival
+    return lat, end
+
+
+def percentiles(values, ps=(50, 99)):
+    v = np.asarray(list(values), dtype=float)
+    return {f"p{p}": float(np.percentile(v, p)) for p in ps}

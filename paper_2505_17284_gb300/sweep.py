@@ -1,0 +1,130 @@
+"""Batched parameter sweeps.
+
+Many independent problems solved together through the batch entry points (one
+launch per stage over the work items of every unfinished problem, replayed as
+a captured CUDA graph while the membership holds), against the same problems
+solved one at a time through the single-problem entry points (create, step to
+N_t, read the QoIs, destroy). The paper's design-parameter studies (Sec. 3.1.3)
+are sweeps of this kind; the paper itself solves them one at a time.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import rt
+
+
+@dataclass
+class Job:
+    """One problem of a sweep: geometry/materials (sn_inputs.Problem), a
+    quadrature (xi, eta, mu, w), the scheme and the target step (0 = default)."""
+    problem: object
+    quad: tuple
+    order: int = 2
+    integrator: int = rt.RT_HEUN
+    dt: float = 0.0
+
+    @property
+    def n_cells(self) -> int:
+        return self.problem.mesh.n_cells
+
+    @property
+    def M(self) -> int:
+        return len(self.quad[0])
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def solve_plain(jobs, storage=rt.RT_FP32, tune=True):
+    """Solve the jobs one after another (a fresh solver each). Returns (QoI
+    dicts, total seconds, seconds per job, steps per job)."""
+    out, per, steps = [], [], []
+    _sync()
+    t0 = time.perf_counter()
+    for j in jobs:
+        a = time.perf_counter()
+        s = rt.Solver(j.problem, j.quad, order=j.order, integrator=j.integrator, storage=storage, dt=j.dt, tune=tune)
+        s.step()
+        out.append(s.qoi())
+        steps.append(int(s.info.n_steps))
+        s.close()
+        per.append(time.perf_counter() - a)
+    _sync()
+    return out, time.perf_counter() - t0, per, steps
+
+
+def solve_batched(jobs, storage=rt.RT_FP32, tile_y=0, phases=None):
+    """Solve the jobs together in one batch. Returns (QoI dicts, seconds from
+    batch creation to the last QoI read, steps per job); `phases`, if a dict,
+    receives the seconds of creation, stepping and read-back."""
+    _sync()
+    t0 = time.perf_counter()
+    b = rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
+                 orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=tile_y)
+    _sync()
+    t1 = time.perf_counter()
+    b.run()
+    _sync()
+    t2 = time.perf_counter()
+    out = [b.qoi(i) for i in range(len(jobs))]
+    b.close()
+    _sync()
+    t3 = time.perf_counter()
+    if phases is not None:
+        phases.update(create=t1 - t0, run=t2 - t1, read_and_destroy=t3 - t2)
+    return out, t3 - t0, [q["n_steps"] for q in out]
+
+
+def tune_batch(jobs, storage=rt.RT_FP32, candidates=(0, 16, 24, 32, 48, 64), steps=4):
+    """Batch-level tuner: the segment length shared by the batch's Cartesian
+    problems, timed with CUDA events over `steps` steps of the whole batch
+    after one warm-up step. Returns (best tile_y, {tile_y: ms per step})."""
+    import torch
+    times = {}
+    for ty in candidates:
+        b = rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
+                     orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=ty)
+        b.step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        b.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        times[ty] = e0.elapsed_time(e1) / steps
+        b.close()
+    best = min(times, key=times.get)
+    return best, times
+
+
+def state_bytes(jobs, steps, storage=rt.RT_FP32, bytes_per_update=None):
+    """Algorithmic HBM bytes of solving the jobs: per cell-ordinate and step,
+    Euler reads psi^n and writes psi^(n+1) (2 values), Heun moves 5 values."""
+    es = 2 if storage == rt.RT_BF16 else 4
+    tot = 0.0
+    for j, n in zip(jobs, steps):
+        per = bytes_per_update if bytes_per_update else (5 if j.integrator == rt.RT_HEUN else 2) * es
+        tot += float(j.n_cells) * j.M * n * per
+    return tot
+
+
+def qoi_rel_diff(a: dict, b: dict) -> float:
+    """Largest relative difference between two results of the final mass and
+    the time-integrated QoIs (absorption per region, boundary outflow), each
+    relative to its own size but at least 1e-3 of the mass, as in the parity
+    tests: a QoI that is still tiny (the outflow before the wave reaches the
+    boundary) carries the rounding of the state near it, not an error of
+    its own."""
+    m = abs(b["mass"])
+    d = abs(a["mass"] - b["mass"]) / max(m, 1e-300)
+    floor = max(1e-3 * m, 1e-300)
+    for x, y in zip(np.atleast_1d(a["abs_int"]), np.atleast_1d(b["abs_int"])):
+        d = max(d, abs(x - y) / max(abs(y), floor))
+    d = max(d, abs(a["outflow_int"] - b["outflow_int"]) / max(abs(b["outflow_int"]), floor))
+    return d

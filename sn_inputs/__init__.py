@@ -343,3 +343,40 @@ def poisson_arrivals(count: int, rate: float, seed: int = 0) -> np.ndarray:
     -log(1-u)/rate from the splitmix64 stream `seed`."""
     u = uniform01(seed, np.arange(count, dtype=np.uint64))
     return np.cumsum(-np.log1p(-u) / rate)
+
+
+@dataclass
+class RequestSpec:
+    """One solve request of the serving stream."""
+    kind: str          # "lattice" (Cartesian, MUSCL, Heun) or "enclosure" (triangles, first order, Euler)
+    n: int
+    n_p: int
+    n_phi: int
+    t_end: float
+
+    @property
+    def M(self) -> int:
+        return self.n_p * self.n_phi
+
+
+SERVE_LATTICE_GRIDS = tuple(range(70, 701, 70))
+SERVE_ENCLOSURE_GRIDS = (130, 260, 390, 520, 650)
+SERVE_MS = (64, 128, 256, 512)
+
+
+def serve_requests(count: int, seed: int = 0, horizon: float = 1.0, lattice_grids=SERVE_LATTICE_GRIDS,
+                   enclosure_grids=SERVE_ENCLOSURE_GRIDS, Ms=SERVE_MS) -> list:
+    """Mixed request stream: request i takes draws 3i..3i+2 of the splitmix64
+    stream `seed` for (kind 50/50, grid, ordinate count). End times are the
+    benchmarks' (lattice 3.2, enclosure 2.6) times `horizon`."""
+    out = []
+    for i in range(count):
+        u = uniform01(seed, np.arange(3 * i, 3 * i + 3, dtype=np.uint64))
+        lattice = u[0] < 0.5
+        grids = lattice_grids if lattice else enclosure_grids
+        n = grids[min(int(u[1] * len(grids)), len(grids) - 1)]
+        M = Ms[min(int(u[2] * len(Ms)), len(Ms) - 1)]
+        n_p, n_phi = QUAD_SHAPES[M]
+        out.append(RequestSpec(kind="lattice" if lattice else "enclosure", n=n, n_p=n_p, n_phi=n_phi,
+                               t_end=(3.2 if lattice else 2.6) * horizon))
+    return out

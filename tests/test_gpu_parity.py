@@ -482,3 +482,46 @@ def test_batch_capacity_and_empty_slots(rt):
     b.step(3)                           # finished problems do not step further
     assert b.progress(slot)[0] == total
     b.close()
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotune_picks_a_buildable_config_that_matches_the_oracle(rt):
+    p = si.lattice_problem(63)
+    p.t_end = 0.6
+    quad = rt.rt_quad_product(8, 32)
+    cfg, ms = rt.rt_autotune(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, steps=3)
+    assert ms > 0
+    assert cfg["tile_x"] in (16, 32) and 1 <= cfg["tile_y"] <= 64 and cfg["variant"] in (1, 2)
+    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, tile_x=cfg["tile_x"],
+                  tile_y=cfg["tile_y"], variant=cfg["variant"], vec=cfg["vec"])
+    assert (s.info.tile_x, s.info.tile_y, s.info.variant, s.info.vec) == \
+        (cfg["tile_x"], cfg["tile_y"], cfg["variant"], cfg["vec"])
+    s.step()
+    psi, q, dt, n = s.psi(), s.qoi(), s.info.dt, s.info.n_steps
+    s.close()
+    op = oracle.CartesianOracle(p, oracle.product_quadrature(8, 32), order=2)
+    ref, acc, S = oracle.run(op, np.zeros((p.mesh.n_cells, 256)), dt, n, "heun")
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_autotune_cache_and_solver_flag(rt, tmp_path, monkeypatch):
+    from paper_2505_17284_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE_PATH", str(tmp_path / "tune.json"))
+    monkeypatch.setattr(autotune, "_mem", None)
+    p = si.lattice_problem(42)
+    quad = rt.rt_quad_product(4, 16)
+    a = autotune.tuned_config(p, quad, 1, rt.RT_EULER, dt=0.5 * p.mesh.dx)
+    assert (tmp_path / "tune.json").exists()
+    b = autotune.tuned_config(p, quad, 1, rt.RT_EULER, dt=0.5 * p.mesh.dx)
+    assert a == b                         # second call from the cache
+    s = rt.Solver(p, quad, order=1, integrator=rt.RT_EULER, dt=0.5 * p.mesh.dx, tune=True)
+    assert (s.info.tile_x, s.info.tile_y) == (a["tile_x"], a["tile_y"])
+    s.close()
+
+
+def test_autotune_rejects_triangles(rt):
+    p = si.enclosure_problem(8, seed=1, t_end=0.2)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_autotune(p, rt.rt_quad_product(2, 8), order=1, integrator=rt.RT_EULER)
+    assert e.value.code == rt.RT_EINVAL

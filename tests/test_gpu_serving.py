@@ -1,0 +1,126 @@
+"""Batched sweeps and the serving loop (continuous batching): each result is
+the same as the problem solved alone, and small served problems match the
+FP64 oracle within the parity tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+import sn_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2505_17284_gb300 import build, rt as rtmod
+    build.build()
+    rtmod.load_library()
+    return rtmod
+
+
+def small_jobs(rt):
+    from paper_2505_17284_gb300.sweep import Job
+    jobs = []
+    for inst in si.sweep_instances(6, seed=4, grids=(21, 28, 35), Ms=(64, 128)):
+        p = si.lattice_problem(inst.n, sigma_a_blue=inst.sigma_a, sigma_s_scatter=inst.sigma_s, t_end=0.8)
+        n_p, n_phi = inst.n_p, inst.n_phi
+        jobs.append(Job(p, rt.rt_quad_product(n_p, n_phi), 2, rt.RT_HEUN, 0.5 * p.mesh.dx))
+    return jobs
+
+
+def test_sweep_batched_equals_one_at_a_time(rt):
+    from paper_2505_17284_gb300 import sweep as S
+    jobs = small_jobs(rt)
+    qb, tb, nb = S.solve_batched(jobs)
+    qp, tp, per, npl = S.solve_plain(jobs, tune=False)
+    assert nb == npl
+    for a, b in zip(qb, qp):
+        for k in a:
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+    best, times = S.tune_batch(jobs, candidates=(0, 8, 16), steps=2)
+    assert best in times and all(t > 0 for t in times.values())
+
+
+def stream(rt, kinds):
+    from paper_2505_17284_gb300.serve import Request, estimate_bytes
+    from paper_2505_17284_gb300.sweep import Job
+    reqs = []
+    for i, (kind, n, n_p, n_phi) in enumerate(kinds):
+        q = rt.rt_quad_product(n_p, n_phi)
+        if kind == "lattice":
+            make = (lambda n=n, q=q: Job(si.lattice_problem(n, t_end=0.6), q, 2, rt.RT_HEUN, 0.5 * 7.0 / n))
+            nb = estimate_bytes(n * n, n_p * n_phi)
+        else:
+            make = (lambda n=n, q=q, i=i: Job(si.enclosure_problem(n, jitter=0.2, seed=i, t_end=0.15), q, 1,
+                                              rt.RT_EULER, 0.0))
+            nb = estimate_bytes(2 * n * n, n_p * n_phi, triangles=True)
+        reqs.append(Request(rid=i, arrival=0.01 * i, make=make, est_bytes=nb))
+    return reqs
+
+
+MIX = [("lattice", 21, 2, 16), ("enclosure", 8, 2, 8), ("lattice", 28, 4, 16), ("enclosure", 10, 4, 16),
+       ("lattice", 14, 2, 8), ("lattice", 35, 8, 16), ("enclosure", 6, 2, 16), ("lattice", 21, 4, 16)]
+
+
+@pytest.mark.parametrize("realtime", [False, True])
+def test_served_results_equal_alone(rt, realtime):
+    """Three slots for eight requests: later requests wait for slots, join the
+    batch while others are mid-solve, and every result is bit-identical to the
+    request solved alone."""
+    from paper_2505_17284_gb300 import serve as SV
+    reqs = stream(rt, MIX)
+    served = SV.Server(capacity=3, chunk=4).run(reqs, realtime=realtime)
+    assert sorted(s.rid for s in served) == list(range(len(MIX)))
+    assert max(s.admitted - s.arrival for s in served) > 0      # some request waited for a slot
+    assert len({s.slot for s in served}) <= 3
+    _, alone = SV.plain_service_times(reqs)
+    for s in served:
+        for k in s.qoi:
+            assert np.array_equal(np.asarray(s.qoi[k]), np.asarray(alone[s.rid][k])), (s.rid, k)
+
+
+def test_served_small_requests_match_the_oracle(rt):
+    from paper_2505_17284_gb300 import serve as SV
+    mix = [("lattice", 14, 2, 8), ("enclosure", 6, 2, 8)]
+    reqs = stream(rt, mix)
+    served = {s.rid: s for s in SV.Server(capacity=2, chunk=3).run(reqs, realtime=False)}
+    for r in reqs:
+        j = r.make()
+        if j.order == 2:
+            op = oracle.CartesianOracle(j.problem, oracle.product_quadrature(2, 8), order=2)
+            n = oracle.n_steps_for(j.problem.t_end, j.dt)
+            dt, integ = j.problem.t_end / n, "heun"
+        else:
+            op = oracle.TriangleOracle(j.problem, oracle.product_quadrature(2, 8))
+            n, dt = oracle.triangle_dt(op, j.problem.t_end)
+            integ = "euler"
+        _, acc, S = oracle.run(op, np.zeros((j.problem.mesh.n_cells, 16)), dt, n, integ)
+        q = served[r.rid].qoi
+        scale = S["mass"]
+        assert q["step"] == n
+        assert abs(q["mass"] - S["mass"]) <= 1e-4 * scale
+        for g in range(len(acc.abs_int)):
+            assert abs(q["abs_int"][g] - acc.abs_int[g]) <= 1e-4 * max(abs(acc.abs_int[g]), 1e-3 * scale)
+        assert abs(q["outflow_int"] - acc.outflow_int) <= 1e-4 * max(abs(acc.outflow_int), 1e-3 * scale)
+
+
+def test_admission_by_memory_budget(rt):
+    """A budget that fits one request at a time serialises the stream; a
+    request larger than the budget is refused with an error."""
+    import torch
+    from paper_2505_17284_gb300 import serve as SV
+    reqs = stream(rt, MIX[:4])
+    free, _ = torch.cuda.mem_get_info()
+    one = max(r.est_bytes for r in reqs)
+    srv = SV.Server(capacity=4, chunk=4, mem_fraction=1.0, reserve=int(free) - int(1.5 * one))
+    served = srv.run(reqs, realtime=False)
+    assert len(served) == 4
+    order = sorted(served, key=lambda s: s.admitted)
+    for a, b in zip(order, order[1:]):
+        assert b.admitted >= a.finished - 1e-9                 # one at a time
+    big = stream(rt, MIX[:1])
+    big[0].est_bytes = int(free) * 2
+    with pytest.raises(RuntimeError):
+        SV.Server(capacity=2).run(big, realtime=False)
