@@ -383,7 +383,8 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   I.n_cells = n_cells;
   I.M = (int32_t)quad->M;
   I.Mpad = (I.M + 31) / 32 * 32;
-  I.vec = I.Mpad >= 128 ? 4 : (I.Mpad >= 64 ? 2 : 1);
+  // ordinates per lane of the cell-range and triangle kernels: 32*vec divides Mpad
+  I.vec = (I.Mpad % 128 == 0) ? 4 : ((I.Mpad % 64 == 0) ? 2 : 1);
   I.t_end = t_end;
   I.n_regions = mat->n_regions;
   const size_t es = storage == RT_BF16 ? 2 : 4;

@@ -74,11 +74,21 @@ struct LaneQoI {
 // Persistent stage kernel: work item g of G processes the 64-cell chunks
 // g, g + G, g + 2G, ... in increasing order, so all SMs sweep the mesh together
 // and the rows of the neighbouring grid row (2n cells away on the split grid)
-// are still in L2 when they are gathered. Warp w takes cells w, w + 8, ... of a
-// chunk, so neighbours one cell apart are fetched by adjacent warps at the same
-// time (L1). QoI terms are summed per warp in shared memory (FP32 over 32
-// cells, then FP64).
+// are still in L2 when they are gathered. The neighbour lists and edge
+// geometry of a chunk (contiguous arrays) are staged in shared memory by two
+// TMA bulk copies, double-buffered one chunk ahead, so a warp starts a cell
+// with its metadata at hand and goes straight to the row loads. Warp w takes
+// cells w, w + 8, ... of a chunk (neighbours one cell apart are fetched by
+// adjacent warps at the same time, L1), and loads the rows of two ordinate
+// blocks before computing either. QoI terms are summed per warp in shared
+// memory (FP32 over 32 cells, then FP64).
 constexpr int kTriChunk = 64;
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
 
 template <int VEC, int STAGE, typename T>
 __global__ void __launch_bounds__(kTriThreads, 3)
@@ -86,6 +96,9 @@ __global__ void __launch_bounds__(kTriThreads, 3)
   __shared__ double red[(kTriWarps + 1) * NQ];
   __shared__ float wacc[kTriWarps][NQ];
   __shared__ double wdacc[kTriWarps][NQ];
+  __shared__ __align__(16) int4 s_nbr[2][kTriChunk];
+  __shared__ __align__(16) float4 s_geo[2][2 * kTriChunk];
+  __shared__ __align__(8) uint64_t s_bar[2];
   const WorkItem it = items[blockIdx.x];
   const InstDesc& d = descs[it.inst];
   InstState* st = d.st;
@@ -106,80 +119,118 @@ __global__ void __launch_bounds__(kTriThreads, 3)
   const int nreg = d.n_regions, nq = nreg + 2;
   const int n_cells = (int)d.n_cells;
   const int n_chunks = (n_cells + kTriChunk - 1) / kTriChunk;
+  const int G = it.b;
+  const int64_t limit = d.wait_limit;
 
+  // metadata of chunk k into buffer b (thread 0)
+  auto stage_meta = [&](int k, int b) {
+    const int c0 = k * kTriChunk;
+    const int cells = min(kTriChunk, n_cells - c0);
+    mbar_arrive_expect_tx(&s_bar[b], (uint32_t)cells * 48u);
+    bulk_load(s_nbr[b], d.tri_nbr + c0, (uint32_t)cells * 16u, &s_bar[b]);
+    bulk_load(s_geo[b], d.tri_geo + 2 * (size_t)c0, (uint32_t)cells * 32u, &s_bar[b]);
+  };
   if (lane < NQ) {
     wacc[warp][lane] = 0.f;
     wdacc[warp][lane] = 0.0;
   }
-  __syncwarp();
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_barrier_init();
+    if (it.a < n_chunks) stage_meta(it.a, 0);
+    if (it.a + G < n_chunks) stage_meta(it.a + G, 1);
+  }
+  __syncthreads();
+  bool ok = true;
   int ncell = 0;
-  for (int k = it.a; k < n_chunks; k += it.b) {
-    const int c_end = min(n_cells, (k + 1) * kTriChunk);
-    for (int cell = k * kTriChunk + warp; cell < c_end; cell += kTriWarps) {
-      const int4 nb = __ldg(&d.tri_nbr[cell]);
-      const float4 g0 = __ldg(&d.tri_geo[2 * (size_t)cell]);
-      const float4 g1 = __ldg(&d.tri_geo[2 * (size_t)cell + 1]);
+  int i = 0;   // chunks done by this CTA
+  for (int k = it.a; k < n_chunks; k += G, ++i) {
+    const int b = i & 1;
+    const bool mok = mbar_wait_bounded(&s_bar[b], (uint32_t)((i >> 1) & 1), limit);
+    if (__syncthreads_or(!mok)) {   // the chunk's metadata never arrived: every warp stops here
+      ok = false;
+      break;
+    }
+    const int c0 = k * kTriChunk;
+    const int c_end = min(n_cells, c0 + kTriChunk);
+    for (int cell = c0 + warp; cell < c_end; cell += kTriWarps) {
+      const int li = cell - c0;
+      const int4 nb = s_nbr[b][li];
+      const float4 g0 = s_geo[b][2 * li], g1 = s_geo[b][2 * li + 1];
       const float ax[3] = {g0.x, g0.z, g1.x};
       const float ay[3] = {g0.y, g0.w, g1.y};
       const int nbr[3] = {nb.x, nb.y, nb.z};
       const int m = nb.w & 255, reg = (nb.w >> 8) & 255;
       const float area = g1.z;
       const float sig_t = d.sig_t[m];
-      const float src = d.sig_s2pi[m] * phi_in[cell] + d.q_src[m];
+      const float phin = phi_in[cell];
       const bool has_bnd = (nbr[0] < 0) | (nbr[1] < 0) | (nbr[2] < 0);
       float gh[3];
 #pragma unroll
       for (int e = 0; e < 3; ++e) gh[e] = (nbr[e] < 0) ? d.ghost[-1 - nbr[e]] : 0.f;
 
       float phi_part = 0.f, bpart = 0.f;
-      for (int v = 0; v < nv; ++v) {
-        const int kk = (v * 32 + lane) * VEC;
-        float c[VEC], nbv[3][VEC], xi[VEC], eta[VEC], w[VEC];
-        load_vec<T, VEC>(psi_in + (size_t)cell * Mpad + kk, c);
+      for (int v0 = 0; v0 < nv; v0 += 2) {
+        // the rows of two ordinate blocks are loaded before either is computed
+        float c2[2][VEC], nbv2[2][3][VEC], base2[2][VEC];
+        const bool two = v0 + 1 < nv;
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          if (nbr[e] >= 0) {
-            load_vec<T, VEC>(psi_in + (size_t)nbr[e] * Mpad + kk, nbv[e]);
-          } else {
-#pragma unroll
-            for (int l = 0; l < VEC; ++l) nbv[e][l] = gh[e];
-          }
-        }
-        load_vec<float, VEC>(d.xi + kk, xi);
-        load_vec<float, VEC>(d.eta + kk, eta);
-        load_vec<float, VEC>(d.w + kk, w);
-        float base[VEC];
-        if constexpr (STAGE == STAGE_HEUN2) load_vec<T, VEC>(psi_base + (size_t)cell * Mpad + kk, base);
-        float out[VEC];
-#pragma unroll
-        for (int l = 0; l < VEC; ++l) {
-          float div = 0.f;
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const int kk = ((v0 + h) * 32 + lane) * VEC;
+          load_vec<T, VEC>(psi_in + (size_t)cell * Mpad + kk, c2[h]);
 #pragma unroll
           for (int e = 0; e < 3; ++e) {
-            const float on = xi[l] * ax[e] + eta[l] * ay[e];
-            div += on * ((on > 0.f) ? c[l] : nbv[e][l]);
+            if (nbr[e] >= 0) {
+              load_vec<T, VEC>(psi_in + (size_t)nbr[e] * Mpad + kk, nbv2[h][e]);
+            } else {
+#pragma unroll
+              for (int l = 0; l < VEC; ++l) nbv2[h][e][l] = gh[e];
+            }
           }
-          const float F = -div - sig_t * c[l] + src;
-          float o;
-          if constexpr (STAGE == STAGE_HEUN2) {
-            o = 0.5f * (base[l] + c[l] + dt * F);
-          } else {
-            o = c[l] + dt * F;
-          }
-          o = Store<T>::round(o);
-          out[l] = o;
-          phi_part += w[l] * o;
-          if (has_bnd) {
+          if constexpr (STAGE == STAGE_HEUN2) load_vec<T, VEC>(psi_base + (size_t)cell * Mpad + kk, base2[h]);
+        }
+        const float src = d.sig_s2pi[m] * phin + d.q_src[m];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const int kk = ((v0 + h) * 32 + lane) * VEC;
+          float xi[VEC], eta[VEC], w[VEC], out[VEC];
+          load_vec<float, VEC>(d.xi + kk, xi);
+          load_vec<float, VEC>(d.eta + kk, eta);
+          load_vec<float, VEC>(d.w + kk, w);
+#pragma unroll
+          for (int l = 0; l < VEC; ++l) {
+            const float c = c2[h][l];
+            float div = 0.f;
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-              if (nbr[e] < 0) {
-                const float on = xi[l] * ax[e] + eta[l] * ay[e];
-                bpart += w[l] * on * ((on > 0.f) ? o : gh[e]);
+              const float on = xi[l] * ax[e] + eta[l] * ay[e];
+              div += on * ((on > 0.f) ? c : nbv2[h][e][l]);
+            }
+            const float F = -div - sig_t * c + src;
+            float o;
+            if constexpr (STAGE == STAGE_HEUN2) {
+              o = 0.5f * (base2[h][l] + c + dt * F);
+            } else {
+              o = c + dt * F;
+            }
+            o = Store<T>::round(o);
+            out[l] = o;
+            phi_part += w[l] * o;
+            if (has_bnd) {
+#pragma unroll
+              for (int e = 0; e < 3; ++e) {
+                if (nbr[e] < 0) {
+                  const float on = xi[l] * ax[e] + eta[l] * ay[e];
+                  bpart += w[l] * on * ((on > 0.f) ? o : gh[e]);
+                }
               }
             }
           }
+          store_vec<T, VEC>(psi_out + (size_t)cell * Mpad + kk, out);
         }
-        store_vec<T, VEC>(psi_out + (size_t)cell * Mpad + kk, out);
       }
       const float ph = warp_sum(phi_part);
       float bsum = 0.f;
@@ -199,6 +250,18 @@ __global__ void __launch_bounds__(kTriThreads, 3)
         __syncwarp();
       }
     }
+    // every warp is done with buffer b: it takes the chunk two ahead
+    __syncthreads();
+    if (threadIdx.x == 0 && k + 2 * G < n_chunks) stage_meta(k + 2 * G, b);
+  }
+  if (!ok && threadIdx.x == 0) {
+    // drain: the metadata copies issued and not consumed (chunks i and i + 1)
+    for (int j = i; j < i + 2; ++j) {
+      const int kj = it.a + j * G;
+      if (kj < n_chunks) mbar_wait_bounded(&s_bar[j & 1], (uint32_t)((j >> 1) & 1), limit);
+    }
+    atomicCAS(&st->status, DEV_OK, DEV_TIMEOUT);
+    st->timeout_where = ((int64_t)blockIdx.x << 32) | (int64_t)i;
   }
   __syncwarp();
   if (lane < nq) wdacc[warp][lane] += (double)wacc[warp][lane];

@@ -221,16 +221,43 @@ def test_enclosure_triangles(rt, integrator):
     check_qoi(q, acc, S, 4, scale=S["mass"] + sum(acc.abs_int))
 
 
-@pytest.mark.parametrize("n_p,n_phi", [(2, 16), (4, 16), (8, 32)])
+@pytest.mark.parametrize("n_p,n_phi", [(2, 16), (4, 16), (8, 32), (6, 16), (16, 32)])
 def test_triangle_random_state_vector_widths(rt, n_p, n_phi):
-    """Random state, one Euler step, ordinate counts 32/64/256 (1, 2 and 4
-    ordinates per lane per access)."""
+    """Random state, one Euler step, ordinate counts 32/64/256/96/512 (1, 2 and
+    4 ordinates per lane per access; 512 is gathered in several ordinate
+    blocks per cell)."""
     p = si.enclosure_problem(18, jitter=0.2, seed=5)
     M = n_p * n_phi
     psi0 = si.random_psi(p.mesh.n_cells, M, seed=2)
     psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, n_p, n_phi, 1, rt.RT_EULER, 1, psi0=psi0)
     assert np.max(np.abs(psi - ref)) <= 2e-6 * np.max(np.abs(ref))
     check_qoi(q, acc, S, 4, scale=S["mass"])
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_triangle_heun_blocks_and_storage(rt, storage):
+    """Heun (stage 2 gathers psi^n beside the neighbour rows) with 512
+    ordinates in several blocks per cell, FP32 and BF16 storage, from a
+    random state over 3 steps."""
+    p = si.enclosure_problem(14, jitter=0.2, seed=9)
+    psi0 = si.random_psi(p.mesh.n_cells, 512, seed=4)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 16, 32, 1, rt.RT_HEUN, 3, psi0=psi0, storage=storage)
+    if storage == 0:
+        assert rel_l2(psi, ref) <= PSI_TOL
+        check_qoi(q, acc, S, 4, scale=S["mass"])
+    else:
+        assert rel_l2(psi, ref) <= 2e-2
+
+
+def test_cartesian_ordinates_not_multiple_of_128(rt):
+    """96 ordinates: the initial-state and conversion kernels take 1 ordinate
+    per lane (32 divides 96, 64 and 128 do not)."""
+    p = si.lattice_problem(21)
+    psi0 = si.random_psi(p.mesh.n_cells, 96, seed=8)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 6, 16, 2, rt.RT_HEUN, 2, psi0=psi0, dt=0.5 * p.mesh.dx)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    assert rel_l2(phi, op.phi(ref)) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
 
 
 def test_lattice_on_triangles(rt):
