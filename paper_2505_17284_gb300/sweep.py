@@ -88,8 +88,13 @@ def tune_batch(jobs, storage=rt.RT_FP32, candidates=(0, 16, 24, 32, 48, 64), ste
     import torch
     times = {}
     for ty in candidates:
-        b = rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
-                     orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=ty)
+        try:
+            b = rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
+                         orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=ty)
+        except rt.RTError as e:
+            if e.code != rt.RT_EINVAL:
+                raise
+            continue   # segment too long for the shared memory of some member
         b.step(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -116,15 +121,17 @@ def state_bytes(jobs, steps, storage=rt.RT_FP32, bytes_per_update=None):
 
 def qoi_rel_diff(a: dict, b: dict) -> float:
     """Largest relative difference between two results of the final mass and
-    the time-integrated QoIs (absorption per region, boundary outflow), each
-    relative to its own size but at least 1e-3 of the mass, as in the parity
-    tests: a QoI that is still tiny (the outflow before the wave reaches the
-    boundary) carries the rounding of the state near it, not an error of
-    its own."""
-    m = abs(b["mass"])
-    d = abs(a["mass"] - b["mass"]) / max(m, 1e-300)
-    floor = max(1e-3 * m, 1e-300)
-    for x, y in zip(np.atleast_1d(a["abs_int"]), np.atleast_1d(b["abs_int"])):
+    the time-integrated QoIs (absorption per region, boundary outflow). Each
+    is relative to its own size but at least 1e-3 of the problem's balance
+    scale max(mass, sum of absorption, |outflow|) (the three terms of the
+    particle balance), as in the parity tests: a QoI that is still tiny (an
+    absorber or boundary the wave has barely reached) carries the rounding of
+    the state near it, not an error of its own."""
+    ai, bi = np.atleast_1d(a["abs_int"]), np.atleast_1d(b["abs_int"])
+    scale = max(abs(b["mass"]), float(np.sum(np.abs(bi))), abs(b["outflow_int"]), 1e-300)
+    floor = 1e-3 * scale
+    d = abs(a["mass"] - b["mass"]) / max(abs(b["mass"]), floor)
+    for x, y in zip(ai, bi):
         d = max(d, abs(x - y) / max(abs(y), floor))
     d = max(d, abs(a["outflow_int"] - b["outflow_int"]) / max(abs(b["outflow_int"]), floor))
     return d
