@@ -215,8 +215,11 @@ def run_ours(args, spec):
     quad = rt.rt_quad_product(n_p, n_phi)
     integ_c = rt.RT_HEUN if integ == "heun" else rt.RT_EULER
     stor_c = rt.RT_BF16 if storage == "bf16" else rt.RT_FP32
+    # Cartesian tiles from the autotuner (timed once per device and shape, before
+    # any timed region) unless given on the command line
+    tune = mesh == "lattice" and not args.no_tune and args.tile_x == 0 and args.tile_y == 0
     solver = rt.Solver(problem, quad, order=order, integrator=integ_c, storage=stor_c, dt=dt,
-                       tile_x=args.tile_x, tile_y=args.tile_y)
+                       tile_x=args.tile_x, tile_y=args.tile_y, tune=tune)
     info = solver.info
     K, W = args.steps, args.warmup
     if K + W > info.n_steps:
@@ -264,7 +267,7 @@ def run_ours(args, spec):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s2 = rt.Solver(problem, quad, order=order, integrator=integ_c, storage=stor_c, dt=dt,
-                   tile_x=args.tile_x, tile_y=args.tile_y)
+                   tile_x=args.tile_x, tile_y=args.tile_y, tune=tune)
     s2.step(K)
     q2 = s2.qoi()
     s2.close()
@@ -288,6 +291,8 @@ def run_ours(args, spec):
                    "cells": n_cells, "ordinates": info.M, "order": order, "integrator": integ,
                    "psi_storage": storage, "dt": info.dt, "n_steps_total": info.n_steps,
                    "tile": [info.tile_x, info.tile_y], "work_items": info.n_work_items,
+                   "tile_choice": "rt_autotune (cached per device and shape)" if tune else
+                                  ("command line" if (args.tile_x or args.tile_y) else "library model"),
                    "l2": f"inputs larger than L2 (psi {dof * (2 if storage == 'bf16' else 4) / 1e9:.2f} GB per buffer)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
@@ -548,6 +553,7 @@ def main():
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="Cartesian tiles from the library's model, not the autotuner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
