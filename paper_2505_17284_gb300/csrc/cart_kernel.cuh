@@ -246,6 +246,7 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const int parity = (STAGE == STAGE_EULER) ? st->parity : 0;
+  [[maybe_unused]] const uint32_t salt = sr_salt(st->step, STAGE);   // BF16 stochastic rounding
   const int in_buf = (STAGE == STAGE_EULER) ? parity : (STAGE == STAGE_HEUN1 ? 0 : 1);
   const int out_buf = (STAGE == STAGE_EULER) ? (1 - parity) : (STAGE == STAGE_HEUN1 ? 1 : 0);
   const float* __restrict__ phi_in = d.phi[in_buf];
@@ -463,7 +464,10 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
             const float div = fmaf(ay[v], g[r][v] - gprev[r][v], dxv);
             float t = fmaf(ta, cj[v], tb) - div;
             if constexpr (STAGE == STAGE_HEUN2) t = 0.5f * (bse[v] + t);
-            t = Store<T>::round(t);
+            if constexpr (sizeof(T) == 2) {
+              const uint32_t rb = sr_bits((int64_t)j * nx + gx, Mpad, (k0 + v) & ~1, salt);
+              t = Store<T>::round_sr(t, ((k0 + v) & 1) ? (rb >> 16) : rb);
+            }
             out[v] = t;
             pw = fmaf(w[v], t, pw);
           }
@@ -591,6 +595,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const int parity = (STAGE == STAGE_EULER) ? st->parity : 0;
+  [[maybe_unused]] const uint32_t salt = sr_salt(st->step, STAGE);   // BF16 stochastic rounding
   const int in_buf = (STAGE == STAGE_EULER) ? parity : (STAGE == STAGE_HEUN1 ? 0 : 1);
   const int out_buf = (STAGE == STAGE_EULER) ? (1 - parity) : (STAGE == STAGE_HEUN1 ? 1 : 0);
   const float* __restrict__ phi_in = d.phi[in_buf];
@@ -799,7 +804,10 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
               const float2 div = __ffma2_rn(ax2[v], sub2(F[r + 1][v], F[r][v]), __fmul2_rn(ay2[v], sub2(X.g[r][v], Y.g[r][v])));
               float2 t = sub2(__ffma2_rn(ta2, Y.c[r][v], tb2), div);
               if constexpr (STAGE == STAGE_HEUN2) t = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(bse[v], t));
-              t = make_float2(Store<T>::round(t.x), Store<T>::round(t.y));
+              if constexpr (sizeof(T) == 2) {
+                const uint32_t rb = sr_bits((int64_t)jrow * nx + (x0 + s0 + DXS * r), Mpad, k0 + 2 * v, salt);
+                t = make_float2(Store<T>::round_sr(t.x, rb), Store<T>::round_sr(t.y, rb >> 16));
+              }
               out[v] = t;
               pw2 = __ffma2_rn(w2[v], t, pw2);
             }

@@ -15,15 +15,50 @@ template <> struct Store<float> {
   static __device__ __forceinline__ float load(const float* p) { return *p; }
   static __device__ __forceinline__ float from_smem(const float v) { return v; }
   static __device__ __forceinline__ float round(float v) { return v; }
+  static __device__ __forceinline__ float round_sr(float v, uint32_t) { return v; }
   static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ float from_smem(const __nv_bfloat16 v) { return __bfloat162float(v); }
-  // round-to-nearest-even to bf16 and back: the value the state will hold
+  // round-to-nearest-even to bf16 and back
   static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+  // stochastic rounding to bf16 and back, with 16 random bits r: the magnitude
+  // is rounded up with probability (dropped low 16 bits) / 2^16, so the stored
+  // value is unbiased; exactly representable values are kept
+  static __device__ __forceinline__ float round_sr(float v, uint32_t r) {
+    return __uint_as_float((__float_as_uint(v) + (r & 0xffffu)) & 0xffff0000u);
+  }
   static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
+
+// ------------------------------------------------------------------ random bits for BF16 stores
+// BF16 keeps 8 significant bits. Rounding every stored state to nearest drops
+// any per-step change smaller than half a unit in the last place; with small
+// time steps (a triangle mesh takes dt from its smallest cells, so most cells
+// change by a small fraction per step) the state then stops moving where it
+// varies slowly and particles are lost. The stage kernels therefore round BF16
+// stores stochastically (Store::round_sr). The random bits are a counter-based
+// hash (Wellons' "lowbias32" 32-bit integer mixer) of the element index
+// (cell * Mpad + ordinate) and a per-stage salt, so a run is reproducible,
+// independent of the launch configuration, and different from step to step.
+__device__ __forceinline__ uint32_t sr_mix(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+// salt of one stage launch: step counter and stage (Euler, Heun 1, Heun 2)
+__device__ __forceinline__ uint32_t sr_salt(int64_t step, int stage) {
+  return sr_mix((uint32_t)step * 4u + (uint32_t)stage + 0x2545f491u);
+}
+// 32 random bits for the element pair (cell, 2p), (cell, 2p + 1): low half for
+// the first, high half for the second
+__device__ __forceinline__ uint32_t sr_bits(int64_t cell, int Mpad, int k, uint32_t salt) {
+  return sr_mix((uint32_t)(cell * (int64_t)Mpad + k) ^ salt);
+}
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kTriThreads, 3)
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int parity = (STAGE == STAGE_EULER) ? st->parity : 0;
+  [[maybe_unused]] const uint32_t salt = sr_salt(st->step, STAGE);   // BF16 stochastic rounding
   const int in_buf = (STAGE == STAGE_EULER) ? parity : (STAGE == STAGE_HEUN1 ? 0 : 1);
   const int out_buf = (STAGE == STAGE_EULER) ? (1 - parity) : (STAGE == STAGE_HEUN1 ? 1 : 0);
   const T* __restrict__ psi_in = reinterpret_cast<const T*>(d.psi[in_buf]);
@@ -216,7 +217,11 @@ __global__ void __launch_bounds__(kTriThreads, 3)
             } else {
               o = c + dt * F;
             }
-            o = Store<T>::round(o);
+            if constexpr (sizeof(T) == 2) {
+              const int ko = kk + l;
+              const uint32_t rb = sr_bits(cell, Mpad, ko & ~1, salt);
+              o = Store<T>::round_sr(o, (ko & 1) ? (rb >> 16) : rb);
+            }
             out[l] = o;
             phi_part += w[l] * o;
             if (has_bnd) {

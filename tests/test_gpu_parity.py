@@ -280,6 +280,36 @@ def test_bf16_storage_error_is_bounded(rt):
     assert rel(q["mass"], S["mass"]) < 1e-2
 
 
+@pytest.mark.parametrize("kind", ["enclosure", "lattice"])
+def test_bf16_small_steps_keep_the_particle_balance(rt, kind):
+    """Many small steps (the triangle time step comes from the smallest cells,
+    so most cells change by a small fraction of a BF16 unit per step): BF16
+    stores round stochastically, so the state keeps moving and the particle
+    balance mass + absorbed + outflow = emitted holds at the BF16 level, and
+    the QoIs stay close to the FP32 run's."""
+    if kind == "enclosure":
+        p = si.enclosure_problem(100, jitter=0.2, seed=2, t_end=0.6)
+        quad, order, integ, dt = rt.rt_quad_product(4, 16), 1, rt.RT_EULER, 0.0
+    else:
+        p = si.lattice_problem(56, t_end=1.6)
+        quad, order, integ, dt = rt.rt_quad_product(4, 16), 2, rt.RT_HEUN, 0.05 * 7.0 / 56
+    res = {}
+    for storage in (rt.RT_FP32, rt.RT_BF16):
+        s = rt.Solver(p, quad, order=order, integrator=integ, storage=storage, dt=dt)
+        s.step()
+        res[storage] = (s.qoi(), s.info.n_steps)
+        s.close()
+    q32, n = res[rt.RT_FP32]
+    q16, _ = res[rt.RT_BF16]
+    assert n >= 100
+    budget = abs(q32["mass"]) + float(np.sum(np.abs(q32["abs_int"]))) + abs(q32["outflow_int"])
+    for q, tol in ((q32, 1e-5), (q16, 2e-3)):
+        bal = q["mass"] + float(np.sum(q["abs_int"])) + q["outflow_int"] - q["source_int"]
+        assert abs(bal) <= tol * budget, (bal, budget)
+    assert rel(q16["mass"], q32["mass"]) < 2e-2
+    assert abs(float(np.sum(q16["abs_int"])) - float(np.sum(q32["abs_int"]))) < 2e-2 * budget
+
+
 # ------------------------------------------------------------------ execution paths
 def test_graph_replay_matches_direct_launches_bitwise(rt):
     p = si.lattice_problem(49)
