@@ -21,12 +21,12 @@ conservation, infinite-medium decay, scattering relaxation, the exact shift,
 discrete mass balance, mirror symmetry of the lattice, convergence orders and
 the paper's own printed lattice QoIs (loosely).
 """
-from .quadrature import product_quadrature, gauss_legendre_01
+from .quadrature import product_quadrature, gauss_legendre_01, tessellation_quadrature
 from .cartesian import CartesianOracle
 from .triangles import TriangleOracle
 from .stepping import run, euler_step, heun_step, n_steps_for, triangle_dt
 
 __all__ = [
-    "product_quadrature", "gauss_legendre_01", "CartesianOracle", "TriangleOracle",
+    "product_quadrature", "gauss_legendre_01", "tessellation_quadrature", "CartesianOracle", "TriangleOracle",
     "run", "euler_step", "heun_step", "n_steps_for", "triangle_dt",
 ]

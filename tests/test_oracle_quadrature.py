@@ -1,12 +1,16 @@
 """Pins for the oracle's product quadrature (Sec. 4.1, Eq. sn_2d and Eq.
 polar_coordinates): weights sum to 2 pi and the rule integrates low-degree
 polynomials of (xi, eta, mu) over the upper hemisphere exactly. The closed
-forms are integrals over [0,1] x [0, 2 pi) in (mu, varphi) computed by hand."""
+forms are integrals over [0,1] x [0, 2 pi) in (mu, varphi) computed by hand.
+The tessellation rule (Sec. 5.1.1) is pinned by its order-1 closed form, the
+tiling of the hemisphere, weights from direct area integration, symmetry and
+moment convergence."""
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 from oracle import product_quadrature, gauss_legendre_01
 
 pytestmark = pytest.mark.filterwarnings("ignore")
@@ -59,3 +63,75 @@ def test_ordinate_ordering_and_mirror_closure():
         b %= n_phi
         assert np.allclose(xi[b * n_p:(b + 1) * n_p], -xi[a * n_p:(a + 1) * n_p], atol=1e-15)
         assert np.allclose(eta[b * n_p:(b + 1) * n_p], eta[a * n_p:(a + 1) * n_p], atol=1e-15)
+
+
+# ------------------------------------------------------------------ tessellation rule (Sec. 5.1.1)
+def test_tessellation_order_one_is_the_octant_centroids():
+    """N = 1: one point per face, the face centre (+-1, +-1, 1)/sqrt(3), with
+    weight the octant's area pi/2."""
+    xi, eta, mu, w = oracle.tessellation_quadrature(1)
+    s = 1.0 / np.sqrt(3.0)
+    assert np.allclose(np.abs(xi), s) and np.allclose(np.abs(eta), s) and np.allclose(mu, s)
+    assert np.allclose(w, np.pi / 2)
+    # quadrants in azimuth order
+    assert list(np.sign(xi)) == [1, -1, -1, 1] and list(np.sign(eta)) == [1, 1, -1, -1]
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 8, 12])
+def test_tessellation_size_tiling_and_quadrant_blocks(N):
+    xi, eta, mu, w = oracle.tessellation_quadrature(N)
+    assert len(w) == 4 * N * N
+    assert abs(w.sum() - 2 * np.pi) < 1e-12          # the spherical triangles tile the hemisphere
+    assert np.all(w > 0) and np.all(mu > 0)
+    assert np.allclose(xi ** 2 + eta ** 2 + mu ** 2, 1.0)
+    sx, sy = np.sign(xi).reshape(4, N * N), np.sign(eta).reshape(4, N * N)
+    for q, (a, b) in enumerate([(1, 1), (-1, 1), (-1, -1), (1, -1)]):
+        assert np.all(sx[q] == a) and np.all(sy[q] == b)
+
+
+def _projected_area(p, q, r, levels=6):
+    """Area on the unit sphere of the central projection of the flat triangle
+    (p, q, r): the integral over the flat triangle of (n . x) / |x|^3 (n the
+    unit normal of its plane), by the midpoint rule on 4^levels sub-triangles."""
+    n = np.cross(q - p, r - p)
+    area2 = np.linalg.norm(n)
+    n = n / area2
+    tris = [(p, q, r)]
+    for _ in range(levels):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nxt += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+        tris = nxt
+    cent = np.array([(a + b + c) / 3 for a, b, c in tris])
+    f = np.abs(cent @ n) / np.linalg.norm(cent, axis=1) ** 3
+    return f.sum() * (area2 / 2) / len(tris)
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_tessellation_weights_are_projected_areas(N):
+    """Each weight equals the area of the projected small triangle computed by
+    direct integration (independent of the spherical-excess formula)."""
+    _, _, _, w = oracle.tessellation_quadrature(N)
+    tris = oracle.quadrature.tessellation_triangles(N)
+    ref = np.array([_projected_area(*t) for t in tris])
+    assert np.max(np.abs(w - ref) / ref) < 2e-4
+
+
+def test_tessellation_symmetry_and_moments():
+    """Mirror and swap symmetries of the point set; second moments exact (the
+    face is symmetric under cyclic permutation of the axes); the fourth moment
+    of mu converges at second order to 2 pi / 5."""
+    for N in (3, 6):
+        xi, eta, mu, w = oracle.tessellation_quadrature(N)
+        P = np.round(np.stack([xi, eta, mu, w], 1), 12)
+        key = lambda A: sorted(map(tuple, A))
+        assert key(P) == key(P[:, [1, 0, 2, 3]])
+        assert key(P) == key(P * np.array([-1, 1, 1, 1]))
+        for v in (xi, eta, mu):
+            assert abs((w * v * v).sum() - 2 * np.pi / 3) < 1e-12
+    err = []
+    for N in (4, 8, 16):
+        xi, eta, mu, w = oracle.tessellation_quadrature(N)
+        err.append(abs((w * mu ** 4).sum() - 2 * np.pi / 5))
+    assert 3.0 < err[0] / err[1] < 5.0 and 3.0 < err[1] / err[2] < 5.0
