@@ -30,7 +30,8 @@ METRIC = "S_N cell-ordinate updates/s"
 UNIT = "updates/s"
 
 WORKLOADS = {
-    # name: (mesh, n, n_p, n_phi, order, integrator, storage, dt_factor, t_end)
+    # name: (mesh, n, n_p, n_phi, order, integrator, storage, dt_factor, t_end); n_p = 0 selects the
+    # tessellation rule of order n_phi (Sec. 5.1.1, 4 n_phi^2 ordinates) instead of the product rule
     "lattice1400_muscl_heun_fp32": ("lattice", 1400, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
     "lattice1400_muscl_heun_bf16": ("lattice", 1400, 16, 32, 2, "heun", "bf16", 0.5, 3.2),
     "lattice1400_o1_euler_fp32": ("lattice", 1400, 16, 32, 1, "euler", "fp32", 0.5, 3.2),
@@ -39,6 +40,8 @@ WORKLOADS = {
     "lattice560_muscl_heun_fp32": ("lattice", 560, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
     "lattice840_muscl_heun_fp32": ("lattice", 840, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
     "enclosure650_tri_o1_euler_fp32": ("enclosure", 650, 8, 32, 1, "euler", "fp32", 0.0, 2.6),
+    # the paper's own angular resolution: tessellation order 22 (1936 ordinates)
+    "lattice1400_muscl_heun_tess22_fp32": ("lattice", 1400, 0, 22, 2, "heun", "fp32", 0.5, 3.2),
 }
 DEFAULT = "lattice1400_muscl_heun_fp32"
 
@@ -154,28 +157,30 @@ import json, sys, time, numpy as np
 sys.path.insert(0, %r)
 import oracle, sn_inputs as si
 mesh, n_full, n_p, n_phi, order, integ, storage, dtf, t_end = %r
+Q = oracle.product_quadrature(n_p, n_phi) if n_p else oracle.tessellation_quadrature(n_phi)
+MQ = len(Q[0])
 budget = %r
 def build(n):
     if mesh == "lattice":
         p = si.lattice_problem(n); dt = dtf * p.mesh.dx
-        op = oracle.CartesianOracle(p, oracle.product_quadrature(n_p, n_phi), order=order)
+        op = oracle.CartesianOracle(p, Q, order=order)
     else:
         p = si.enclosure_problem(n, jitter=0.2, seed=0)
-        op = oracle.TriangleOracle(p, oracle.product_quadrature(n_p, n_phi))
+        op = oracle.TriangleOracle(p, Q)
         dt = oracle.triangle_dt(op, t_end)[1]
     return p, op, dt
 n = 14 if mesh == "lattice" else 10
 p, op, dt = build(n)
-psi = np.zeros((p.mesh.n_cells, n_p * n_phi))
+psi = np.zeros((p.mesh.n_cells, MQ))
 t0 = time.perf_counter(); oracle.run(op, psi, dt, 1, integ); t1 = time.perf_counter()
-rate = p.mesh.n_cells * n_p * n_phi / (t1 - t0)
+rate = p.mesh.n_cells * MQ / (t1 - t0)
 steps = 3
-n2 = int(max(14, min(n_full, (rate * budget / steps / (n_p * n_phi)) ** 0.5 / (1 if mesh == "lattice" else 1.41))))
+n2 = int(max(14, min(n_full, (rate * budget / steps / MQ) ** 0.5 / (1 if mesh == "lattice" else 1.41))))
 if mesh == "lattice": n2 = max(7, n2 // 7 * 7)
 p, op, dt = build(n2)
-psi = np.zeros((p.mesh.n_cells, n_p * n_phi))
+psi = np.zeros((p.mesh.n_cells, MQ))
 t0 = time.perf_counter(); oracle.run(op, psi, dt, steps, integ); t1 = time.perf_counter()
-print(json.dumps({"rate": p.mesh.n_cells * n_p * n_phi * steps / (t1 - t0), "n": n2, "steps": steps,
+print(json.dumps({"rate": p.mesh.n_cells * MQ * steps / (t1 - t0), "n": n2, "steps": steps,
                   "cells": p.mesh.n_cells, "seconds": t1 - t0}))
 """ % (ROOT, list(spec), budget_s)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -185,7 +190,7 @@ print(json.dumps({"rate": p.mesh.n_cells * n_p * n_phi * steps / (t1 - t0), "n":
     d = json.loads(r.stdout.strip().splitlines()[-1])
     mesh = spec[0]
     desc = (f"FP64 numpy oracle, 1 thread: {'lattice' if mesh == 'lattice' else 'enclosure triangles'} "
-            f"{d['n']}x{d['n']} ({d['cells']} cells) x {spec[2] * spec[3]} ordinates, {d['steps']} steps of the "
+            f"{d['n']}x{d['n']} ({d['cells']} cells) x {spec[2] * spec[3] if spec[2] else 4 * spec[3] ** 2} ordinates, {d['steps']} steps of the "
             f"same scheme; rate scaled per cell-ordinate update")
     return d["rate"], desc, d["seconds"]
 
@@ -212,7 +217,7 @@ def run_ours(args, spec):
 
     mesh, n, n_p, n_phi, order, integ, storage, dtf, t_end = spec
     problem, dt = make_problem(spec)
-    quad = rt.rt_quad_product(n_p, n_phi)
+    quad = rt.rt_quad_product(n_p, n_phi) if n_p else rt.rt_quad_tessellation(n_phi)
     integ_c = rt.RT_HEUN if integ == "heun" else rt.RT_EULER
     stor_c = rt.RT_BF16 if storage == "bf16" else rt.RT_FP32
     # Cartesian tiles from the autotuner (timed once per device and shape, before
@@ -329,17 +334,18 @@ def run_reference(args, spec):
     import oracle
     import sn_inputs as si
     mesh, n_full, n_p, n_phi, order, integ, storage, dtf, t_end = spec
+    Q = oracle.product_quadrature(n_p, n_phi) if n_p else oracle.tessellation_quadrature(n_phi)
     # size the sample so that one step costs about per_step seconds
     def build(n):
         if mesh == "lattice":
             p = si.lattice_problem(n)
-            op = oracle.CartesianOracle(p, oracle.product_quadrature(n_p, n_phi), order=order)
+            op = oracle.CartesianOracle(p, Q, order=order)
             return p, op, dtf * p.mesh.dx
         p = si.enclosure_problem(n, jitter=0.2, seed=0)
-        op = oracle.TriangleOracle(p, oracle.product_quadrature(n_p, n_phi))
+        op = oracle.TriangleOracle(p, Q)
         return p, op, oracle.triangle_dt(op, t_end)[1]
     p, op, dt = build(14 if mesh == "lattice" else 10)
-    M = n_p * n_phi
+    M = len(Q[0])
     t0 = time.perf_counter()
     oracle.run(op, np.zeros((p.mesh.n_cells, M)), dt, 1, integ)
     rate = p.mesh.n_cells * M / (time.perf_counter() - t0)

@@ -195,6 +195,19 @@ typedef struct rt_solver rt_solver;
  * RT_EINVAL if n_p < 1, n_p > 64, n_phi < 1 or an output pointer is NULL. */
 rt_status rt_quad_product(int32_t n_p, int32_t n_phi, double* xi, double* eta, double* mu, double* w);
 
+/* Tessellation quadrature of order N (Sec. 5.1.1, the paper's own choice): each
+ * of the four upper faces of the octahedron with vertices (+-1,0,0), (0,+-1,0),
+ * (0,0,1) is split into N^2 congruent triangles by dividing its edges into N
+ * parts; a triangle's ordinate is its centroid scaled to the unit sphere and
+ * its weight the area of the spherical triangle spanned by its corners scaled
+ * to the sphere (spherical excess), so the weights sum to 2 pi. M = 4 N^2
+ * ordinates in face order (the quadrants xi>0,eta>0; xi<0,eta>0; xi<0,eta<0;
+ * xi>0,eta<0, N^2 each); within a face, rows j = 0..N-1 from the equator up and
+ * in each row i = 0..N-1-j the upward triangle (i,j), then, if i < N-1-j, the
+ * downward one. Writes M values to each host array (mu may be NULL). RT_EINVAL
+ * if N < 1, N > 128 or an output pointer is NULL. */
+rt_status rt_quad_tessellation(int32_t N, double* xi, double* eta, double* mu, double* w);
+
 /* Create a solver for one problem: validates, derives per-cell metadata
  * (triangles: areas, n*l/A per edge, neighbours, boundary sides), allocates
  * device state, sets psi(0) = 0 and evaluates phi and the QoI integrands of the

@@ -72,3 +72,57 @@ extern "C" rt_status rt_quad_product(int32_t n_p, int32_t n_phi, double* xi, dou
   }
   return RT_OK;
 }
+
+namespace {
+
+struct Vec3 {
+  double x, y, z;
+};
+Vec3 add(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+Vec3 scale(Vec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+Vec3 unit(Vec3 a) { return scale(a, 1.0 / std::sqrt(dot(a, a))); }
+
+// Area of the spherical triangle with unit corners a, b, c: twice the angle of
+// the complex number (1 + a.b + b.c + c.a) + i |a.(b x c)|.
+double excess(Vec3 a, Vec3 b, Vec3 c) {
+  const Vec3 bc = {b.y * c.z - b.z * c.y, b.z * c.x - b.x * c.z, b.x * c.y - b.y * c.x};
+  const double num = std::fabs(dot(a, bc));
+  const double den = 1.0 + dot(a, b) + dot(b, c) + dot(c, a);
+  return 2.0 * std::atan2(num, den);
+}
+
+}  // namespace
+
+extern "C" rt_status rt_quad_tessellation(int32_t N, double* xi, double* eta, double* mu, double* w) {
+  rtk::clear_error();
+  if (N < 1 || N > 128 || !xi || !eta || !w) {
+    rtk::set_error("rt_quad_tessellation: need 1 <= N <= 128 and output arrays");
+    return RT_EINVAL;
+  }
+  // upper faces of the octahedron, one per azimuth quadrant: corners A, B, pole
+  const Vec3 corner[5] = {{1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}, {1, 0, 0}};
+  const Vec3 pole = {0, 0, 1};
+  int k = 0;
+  for (int f = 0; f < 4; ++f) {
+    const Vec3 A = corner[f], B = corner[f + 1];
+    auto P = [&](int i, int j) {   // A + (B - A) i/N + (pole - A) j/N
+      const double u = (double)i / N, v = (double)j / N;
+      return add(add(scale(A, 1.0 - u - v), scale(B, u)), scale(pole, v));
+    };
+    auto emit = [&](Vec3 p, Vec3 q, Vec3 r) {
+      const Vec3 c = unit(scale(add(add(p, q), r), 1.0 / 3.0));
+      xi[k] = c.x;
+      eta[k] = c.y;
+      if (mu) mu[k] = c.z;
+      w[k] = excess(unit(p), unit(q), unit(r));
+      ++k;
+    };
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N - j; ++i) {
+        emit(P(i, j), P(i + 1, j), P(i, j + 1));
+        if (i < N - 1 - j) emit(P(i + 1, j), P(i + 1, j + 1), P(i, j + 1));
+      }
+  }
+  return RT_OK;
+}

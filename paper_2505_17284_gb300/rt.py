@@ -105,6 +105,7 @@ class rt_cart_stage_args(C.Structure):
 # exported functions: name -> (restype, argtypes)
 SIGNATURES = {
     "rt_quad_product": (C.c_int, [C.c_int32, C.c_int32, _dp, _dp, _dp, _dp]),
+    "rt_quad_tessellation": (C.c_int, [C.c_int32, _dp, _dp, _dp, _dp]),
     "rt_create": (C.c_int, [C.POINTER(rt_mesh), C.POINTER(rt_materials), C.POINTER(rt_quadrature),
                             C.POINTER(rt_boundary), C.POINTER(rt_options), C.POINTER(C.c_void_p)]),
     "rt_step": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -177,6 +178,13 @@ def rt_quad_product(n_p: int, n_phi: int):
     M = n_p * n_phi
     xi, eta, mu, w = (np.zeros(M) for _ in range(4))
     check(_fns().rt_quad_product(n_p, n_phi, _ptr(xi), _ptr(eta), _ptr(mu), _ptr(w)))
+    return xi, eta, mu, w
+
+
+def rt_quad_tessellation(N: int):
+    M = 4 * N * N
+    xi, eta, mu, w = (np.zeros(M) for _ in range(4))
+    check(_fns().rt_quad_tessellation(N, _ptr(xi), _ptr(eta), _ptr(mu), _ptr(w)))
     return xi, eta, mu, w
 
 

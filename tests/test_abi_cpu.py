@@ -56,6 +56,17 @@ def test_quad_product_rejects_bad_sizes(rt):
         rt.rt_quad_product(65, 8)
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 8, 22])
+def test_quad_tessellation_matches_oracle(rt, N):
+    xi, eta, mu, w = rt.rt_quad_tessellation(N)
+    oxi, oeta, omu, ow = oracle.tessellation_quadrature(N)
+    for a, b in ((xi, oxi), (eta, oeta), (mu, omu), (w, ow)):
+        assert np.max(np.abs(a - b)) < 5e-14
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_quad_tessellation(0)
+    assert e.value.code == rt.RT_EINVAL
+
+
 def _create(rt, problem, quad, **kw):
     keep = rt._Keep()
     mesh, mat, q, bc = rt.make_structs(problem, quad, keep)

@@ -582,3 +582,40 @@ def test_autotune_rejects_triangles(rt):
     with pytest.raises(rt.RTError) as e:
         rt.rt_autotune(p, rt.rt_quad_product(2, 8), order=1, integrator=rt.RT_EULER)
     assert e.value.code == rt.RT_EINVAL
+
+
+# ------------------------------------------------------------------ tessellation quadrature (Sec. 5.1.1)
+@pytest.mark.parametrize("N,n", [(4, 63), (8, 63), (22, 28)])
+def test_tessellation_quadrature_cartesian(rt, N, n):
+    """The paper's tessellation rule (64, 256 and 1936 ordinates: per-lane,
+    32-cell chunk-uniform and 1-ordinate-per-lane kernels), MUSCL Heun from a
+    smooth state against the oracle."""
+    p = si.lattice_problem(n)
+    M = 4 * N * N
+    psi0 = si.smooth_psi(p.mesh, M, seed=6)
+    quad = rt.rt_quad_tessellation(N)
+    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    s.set_psi(psi0)
+    steps = 4
+    s.step(steps)
+    psi, q, dt = s.psi(), s.qoi(), s.info.dt
+    s.close()
+    op = oracle.CartesianOracle(p, oracle.tessellation_quadrature(N), order=2)
+    ref, acc, S = oracle.run(op, psi0, dt, steps, "heun")
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_tessellation_quadrature_triangles(rt):
+    p = si.enclosure_problem(20, jitter=0.2, seed=3)
+    quad = rt.rt_quad_tessellation(4)
+    psi0 = si.random_psi(p.mesh.n_cells, 64, seed=9)
+    s = rt.Solver(p, quad, order=1, integrator=rt.RT_EULER)
+    s.set_psi(psi0)
+    s.step(5)
+    psi, q, dt = s.psi(), s.qoi(), s.info.dt
+    s.close()
+    op = oracle.TriangleOracle(p, oracle.tessellation_quadrature(4))
+    ref, acc, S = oracle.run(op, psi0, dt, 5, "euler")
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 4, scale=S["mass"])
