@@ -183,6 +183,12 @@ typedef struct {
   int64_t device_bytes;
   int32_t variant;   /* Cartesian kernel variant in use: 1 per-lane, 2 chunk-uniform (0: triangles) */
   int32_t vec;       /* ordinates per lane */
+  int32_t regrouped; /* Cartesian: 1 if the ordinates are stored regrouped by direction quadrant, each
+                        quadrant padded with zero-weight ordinates to whole chunks (done when the
+                        caller's order does not give sign-uniform chunks and the padding adds at most
+                        1/8; M_pad is then the padded count). rt_get_psi / rt_set_psi always use the
+                        caller's order; rt_device_state exposes the internal one. */
+  int32_t pad;
 } rt_info_t;
 
 typedef struct rt_solver rt_solver;
@@ -239,7 +245,8 @@ rt_status rt_get_phi(rt_solver* s, double* host, int64_t n);
  * time integrals are kept. Synchronises. */
 rt_status rt_set_psi(rt_solver* s, const double* host, int64_t n);
 
-/* Device view of the current state: psi (storage type, [cell][M_pad]) and phi
+/* Device view of the current state: psi (storage type, [cell][M_pad], ordinates
+ * in the internal order: the caller's unless rt_info_t.regrouped) and phi
  * (float, [cell]). Pointers stay owned by the solver and are valid until the
  * next rt_step (Euler alternates two buffers) or rt_destroy. */
 rt_status rt_device_state(rt_solver* s, void** psi, void** phi, int32_t* storage);

@@ -200,6 +200,7 @@ rt_status rt_info(const rt_solver* s, rt_info_t* out) {
   out->device_bytes = s->arena.bytes;
   out->variant = I.kind == RT_MESH_CARTESIAN ? (I.uni ? 2 : 1) : 0;
   out->vec = I.kind == RT_MESH_CARTESIAN ? I.cvec : I.vec;
+  out->regrouped = I.regrouped;
   return RT_OK;
 }
 

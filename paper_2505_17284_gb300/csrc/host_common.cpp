@@ -307,6 +307,55 @@ static int cart_ctas_per_sm(const Instance& I, int ly) {
   return std::max(1, std::min(by_regs, by_smem));
 }
 
+// Ordinates regrouped by direction quadrant (xi >= 0 and eta >= 0 first, then
+// the quadrants in azimuth order; zeros count as positive), each quadrant padded
+// with zero-weight ordinates to whole chunks of C = 128 (or 64) ordinates, when
+// the caller's order does not already give sign-uniform chunks and the padding
+// costs at most 1/8 more ordinates. Then the chunk-uniform Cartesian kernel
+// applies to any quadrature whose quadrants are about chunk-sized multiples
+// (the tessellation rule of Sec. 5.1.1, for instance). Fills the regrouped
+// arrays (pads: xi = eta = w = 0) and the maps; false: keep the caller's order.
+static bool regroup_quadrature(const rt_quadrature* quad, std::vector<double>& xi, std::vector<double>& eta,
+                               std::vector<double>& w, std::vector<int32_t>& kmap, std::vector<int32_t>& inv) {
+  const int M = (int)quad->M;
+  const int Mpad = (M + 31) / 32 * 32;
+  int8_t dx[kMaxUniChunks], dy[kMaxUniChunks];
+  for (int V = 4; V >= 2; V /= 2)
+    if (Mpad % (32 * V) == 0 && chunks_uniform(quad, Mpad, V, dx, dy)) return false;   // already uniform
+  auto quadrant = [&](int k) {
+    const bool xp = quad->xi[k] >= 0.0, yp = quad->eta[k] >= 0.0;
+    return xp ? (yp ? 0 : 3) : (yp ? 1 : 2);
+  };
+  int count[4] = {0, 0, 0, 0};
+  for (int k = 0; k < M; ++k) ++count[quadrant(k)];
+  for (int C : {128, 64}) {
+    int total = 0;
+    for (int q = 0; q < 4; ++q) total += (count[q] + C - 1) / C * C;
+    if (total > Mpad + Mpad / 8 || total / C > kMaxUniChunks) continue;
+    xi.assign(total, 0.0);
+    eta.assign(total, 0.0);
+    w.assign(total, 0.0);
+    kmap.assign(M, -1);
+    inv.assign(total, -1);
+    int base = 0;
+    for (int q = 0; q < 4; ++q) {
+      int slot = base;
+      for (int k = 0; k < M; ++k)
+        if (quadrant(k) == q) {
+          xi[slot] = quad->xi[k];
+          eta[slot] = quad->eta[k];
+          w[slot] = quad->w[k];
+          kmap[k] = slot;
+          inv[slot] = k;
+          ++slot;
+        }
+      base += (count[q] + C - 1) / C * C;
+    }
+    return true;
+  }
+  return false;
+}
+
 static void choose_cart_tiles(Instance& I, int tile_y) {
   I.tx = cart_tile_width(I.run);
   I.n_strips = (I.nx + I.tx - 1) / I.tx;
@@ -382,7 +431,22 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   I.kind = mesh->kind; I.order = order; I.integrator = integrator; I.storage = storage;
   I.n_cells = n_cells;
   I.M = (int32_t)quad->M;
-  I.Mpad = (I.M + 31) / 32 * 32;
+  // Cartesian meshes: ordinates regrouped by quadrant when that gives sign-uniform
+  // chunks; from here on `quad` is the internal layout (I.M stays the caller's count)
+  std::vector<double> rq_xi, rq_eta, rq_w;
+  std::vector<int32_t> rq_kmap, rq_inv;
+  rt_quadrature rq{};
+  I.regrouped = 0;
+  if (mesh->kind == RT_MESH_CARTESIAN && variant != 1 &&
+      regroup_quadrature(quad, rq_xi, rq_eta, rq_w, rq_kmap, rq_inv)) {
+    rq.M = (int64_t)rq_xi.size();
+    rq.xi = rq_xi.data();
+    rq.eta = rq_eta.data();
+    rq.w = rq_w.data();
+    quad = &rq;
+    I.regrouped = 1;
+  }
+  I.Mpad = (int32_t)((quad->M + 31) / 32 * 32);
   // ordinates per lane of the cell-range and triangle kernels: 32*vec divides Mpad
   I.vec = (I.Mpad % 128 == 0) ? 4 : ((I.Mpad % 64 == 0) ? 2 : 1);
   I.t_end = t_end;
@@ -509,7 +573,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   keep.emplace_back(3 * (size_t)I.Mpad * sizeof(float));
   float* hq = reinterpret_cast<float*>(keep.back().data());
   for (int k = 0; k < I.Mpad; ++k) {
-    const bool in = k < I.M;
+    const bool in = k < quad->M;
     hq[k] = in ? (float)quad->xi[k] : 0.f;
     hq[I.Mpad + k] = in ? (float)quad->eta[k] : 0.f;
     hq[2 * I.Mpad + k] = in ? (float)quad->w[k] : 0.f;
@@ -518,6 +582,18 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   if ((s = arena.get(3 * (size_t)I.Mpad * sizeof(float), &p)) != RT_OK) return s;
   d_quad = (float*)p;
   RT_CUDA_TRY(cudaMemcpyAsync(d_quad, hq, 3 * (size_t)I.Mpad * sizeof(float), cudaMemcpyHostToDevice, stream));
+  I.kmap = I.inv = nullptr;
+  if (I.regrouped) {
+    // caller <-> internal ordinate maps for psi input and output
+    keep.emplace_back(((size_t)I.M + I.Mpad) * sizeof(int32_t));
+    int32_t* hm = reinterpret_cast<int32_t*>(keep.back().data());
+    for (int k = 0; k < I.M; ++k) hm[k] = rq_kmap[k];
+    for (int k = 0; k < I.Mpad; ++k) hm[I.M + k] = k < (int)rq_inv.size() ? rq_inv[k] : -1;
+    if ((s = arena.get(((size_t)I.M + I.Mpad) * sizeof(int32_t), &p)) != RT_OK) return s;
+    I.kmap = (int32_t*)p;
+    I.inv = I.kmap + I.M;
+    RT_CUDA_TRY(cudaMemcpyAsync(I.kmap, hm, ((size_t)I.M + I.Mpad) * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+  }
 
   uint8_t* d_mat = nullptr;
   uint8_t* d_reg = nullptr;
@@ -678,7 +754,7 @@ rt_status copy_psi_out(const Instance& I, DeviceArena& arena, cudaStream_t strea
   for (int64_t c0 = 0; c0 < I.n_cells; c0 += chunk) {
     const int64_t nc = std::min(chunk, I.n_cells - c0);
     const char* src = (const char*)I.psi[buf] + (size_t)c0 * I.Mpad * es;
-    cudaError_t e = launch_convert_out(src, (double*)tmp, nc, I.M, I.Mpad, I.storage, stream);
+    cudaError_t e = launch_convert_out(src, (double*)tmp, nc, I.M, I.Mpad, I.storage, I.kmap, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host + c0 * I.M, tmp, (size_t)nc * I.M * 8, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
@@ -701,7 +777,7 @@ rt_status copy_psi_in(const Instance& I, DeviceArena& arena, cudaStream_t stream
     const int64_t nc = std::min(chunk, I.n_cells - c0);
     char* dst = (char*)I.psi[buf] + (size_t)c0 * I.Mpad * es;
     cudaError_t e = cudaMemcpyAsync(tmp, host + c0 * I.M, (size_t)nc * I.M * 8, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = launch_convert_in((const double*)tmp, dst, nc, I.M, I.Mpad, I.storage, stream);
+    if (e == cudaSuccess) e = launch_convert_in((const double*)tmp, dst, nc, I.M, I.Mpad, I.storage, I.inv, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
       arena.release(tmp);

@@ -49,6 +49,12 @@ struct Instance {
   int32_t tx = 16, ly = 32, n_strips = 0, n_segs = 0;
   int32_t run = 2, cvec = 1;        // Cartesian kernel: cells per thread, ordinates per lane
   int32_t uni = 0;                  // Cartesian kernel: chunk-uniform flow directions
+  // ordinate layout: 0 the caller's order; 1 regrouped by direction quadrant,
+  // each quadrant padded to whole chunks (kmap: caller k -> slot; inv: slot ->
+  // caller k or -1; device arrays, NULL for the caller's order)
+  int32_t regrouped = 0;
+  int32_t* kmap = nullptr;
+  int32_t* inv = nullptr;
   int32_t n_regions = 0;
   double source_rate = 0;   // 2 pi sum_i A_i Q_i
   size_t cart_smem = 0;

@@ -103,9 +103,12 @@ cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, in
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
+// FP64 [cell][M] (caller's ordinate order) <-> storage [cell][Mpad] (internal
+// order); inv: internal slot -> caller ordinate or -1, kmap: caller ordinate ->
+// slot (device arrays; NULL when the orders agree).
 cudaError_t launch_convert_in(const double* src, void* dst, int64_t n_cells, int M, int Mpad, int storage,
-                              cudaStream_t stream);
+                              const int32_t* inv, cudaStream_t stream);
 cudaError_t launch_convert_out(const void* src, double* dst, int64_t n_cells, int M, int Mpad, int storage,
-                               cudaStream_t stream);
+                               const int32_t* kmap, cudaStream_t stream);
 
 }  // namespace rtk

@@ -416,48 +416,49 @@ cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_i
 // layout [cell][Mpad] of T (round to nearest even for bf16; padding zeroed).
 template <typename T>
 __global__ void convert_in_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n_cells, int M,
-                                  int Mpad) {
+                                  int Mpad, const int32_t* __restrict__ inv) {
   const int64_t n = n_cells * Mpad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = i / Mpad;
-    const int k = (int)(i - cell * Mpad);
-    const float v = (k < M) ? (float)src[cell * M + k] : 0.f;
+    const int slot = (int)(i - cell * Mpad);
+    const int k = inv ? inv[slot] : (slot < M ? slot : -1);
+    const float v = (k >= 0) ? (float)src[cell * M + k] : 0.f;
     Store<T>::store(dst + i, v);
   }
 }
 
 template <typename T>
 __global__ void convert_out_kernel(const T* __restrict__ src, double* __restrict__ dst, int64_t n_cells, int M,
-                                   int Mpad) {
+                                   int Mpad, const int32_t* __restrict__ kmap) {
   const int64_t n = n_cells * M;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cell = i / M;
     const int k = (int)(i - cell * M);
-    dst[i] = (double)Store<T>::load(src + cell * Mpad + k);
+    dst[i] = (double)Store<T>::load(src + cell * Mpad + (kmap ? kmap[k] : k));
   }
 }
 
 cudaError_t launch_convert_in(const double* src, void* dst, int64_t n_cells, int M, int Mpad, int storage,
-                              cudaStream_t s) {
+                              const int32_t* inv, cudaStream_t s) {
   const int64_t n = n_cells * Mpad;
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (n == 0) return cudaSuccess;
   if (storage == 0)
-    convert_in_kernel<float><<<blocks, 256, 0, s>>>(src, (float*)dst, n_cells, M, Mpad);
+    convert_in_kernel<float><<<blocks, 256, 0, s>>>(src, (float*)dst, n_cells, M, Mpad, inv);
   else
-    convert_in_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n_cells, M, Mpad);
+    convert_in_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n_cells, M, Mpad, inv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert_out(const void* src, double* dst, int64_t n_cells, int M, int Mpad, int storage,
-                               cudaStream_t s) {
+                               const int32_t* kmap, cudaStream_t s) {
   const int64_t n = n_cells * M;
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (n == 0) return cudaSuccess;
   if (storage == 0)
-    convert_out_kernel<float><<<blocks, 256, 0, s>>>((const float*)src, dst, n_cells, M, Mpad);
+    convert_out_kernel<float><<<blocks, 256, 0, s>>>((const float*)src, dst, n_cells, M, Mpad, kmap);
   else
-    convert_out_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)src, dst, n_cells, M, Mpad);
+    convert_out_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)src, dst, n_cells, M, Mpad, kmap);
   return cudaGetLastError();
 }
 

@@ -77,7 +77,7 @@ class rt_info_t(C.Structure):
                 ("kind", C.c_int32), ("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("n_work_items", C.c_int32),
                 ("stages_per_step", C.c_int32), ("device_bytes", C.c_int64), ("variant", C.c_int32),
-                ("vec", C.c_int32)]
+                ("vec", C.c_int32), ("regrouped", C.c_int32), ("pad", C.c_int32)]
 
 
 class rt_problem(C.Structure):

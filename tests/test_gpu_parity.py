@@ -595,7 +595,10 @@ def test_tessellation_quadrature_cartesian(rt, N, n):
     psi0 = si.smooth_psi(p.mesh, M, seed=6)
     quad = rt.rt_quad_tessellation(N)
     s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    # 484 ordinates per quadrant: stored regrouped, each quadrant padded to 512
+    assert s.info.regrouped == (N == 22) and (N != 22 or (s.info.M_pad == 2048 and s.info.variant == 2))
     s.set_psi(psi0)
+    assert np.array_equal(s.psi(), psi0.astype(np.float32).astype(np.float64))   # caller's order both ways
     steps = 4
     s.step(steps)
     psi, q, dt = s.psi(), s.qoi(), s.info.dt
@@ -619,3 +622,33 @@ def test_tessellation_quadrature_triangles(rt):
     ref, acc, S = oracle.run(op, psi0, dt, 5, "euler")
     assert rel_l2(psi, ref) <= PSI_TOL
     check_qoi(q, acc, S, 4, scale=S["mass"])
+
+
+def test_regrouped_product_quadrature(rt):
+    """12 x 40 product rule: 120 ordinates per quadrant, so chunks of the
+    caller's order mix signs; stored regrouped (quadrants padded to 128) and
+    run on the chunk-uniform kernel, against the oracle; psi round-trips in the
+    caller's order and a checkpoint resumes bit for bit."""
+    p = si.lattice_problem(28)
+    quad = rt.rt_quad_product(12, 40)
+    psi0 = si.smooth_psi(p.mesh, 480, seed=2)
+    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    assert s.info.regrouped == 1 and s.info.M_pad == 512 and s.info.variant == 2
+    s.set_psi(psi0)
+    s.step(2)
+    blob = rt.rt_get_state(s.h)
+    s.step(2)
+    psi, q, dt = s.psi(), s.qoi(), s.info.dt
+    s.close()
+    b = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    rt.rt_set_state(b.h, blob)
+    b.step(2)
+    assert np.array_equal(b.psi(), psi)
+    b.close()
+    op = oracle.CartesianOracle(p, oracle.product_quadrature(12, 40), order=2)
+    ref, acc, S = oracle.run(op, psi0, dt, 4, "heun")
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+    lane = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, variant=1)
+    assert lane.info.regrouped == 0          # the per-lane kernel keeps the caller's order
+    lane.close()
