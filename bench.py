@@ -375,6 +375,8 @@ EXTRA_WORKLOADS = {
     "sweep256": dict(kind="sweep", k=256, grids=(70, 140, 280, 560)),
     # the same draws restricted to small grids, where one solve cannot fill the GPU
     "sweep256_small": dict(kind="sweep", k=256, grids=(70, 140)),
+    # lattice DP-2 sweep: 256 instances, 49 per-block sigma_a and sigma_s each, same grids and ordinates
+    "sweep256_dp2": dict(kind="sweep", k=256, grids=(70, 140, 280, 560), dp=2),
     # Poisson stream of 200 mixed lattice / enclosure requests, end times x 0.1
     "serve200": dict(kind="serve", count=200, horizon=0.1),
 }
@@ -387,10 +389,15 @@ def _quads(rt, cache, n_p, n_phi):
     return cache[key]
 
 
-def sweep_jobs(rt, k, grids, seed=0):
+def sweep_jobs(rt, k, grids, seed=0, dp=1):
     import sn_inputs as si
     from paper_2505_17284_gb300.sweep import Job
     qc, jobs = {}, []
+    if dp == 2:
+        for inst in si.dp2_instances(k, seed, grids=grids):
+            p = si.lattice_dp2_problem(inst.n, inst.sigma_a, inst.sigma_s)
+            jobs.append(Job(p, _quads(rt, qc, inst.n_p, inst.n_phi), 2, rt.RT_HEUN, 0.5 * p.mesh.dx))
+        return jobs
     for inst in si.sweep_instances(k, seed, grids=grids):
         p = si.lattice_problem(inst.n, sigma_a_blue=inst.sigma_a, sigma_s_scatter=inst.sigma_s)
         jobs.append(Job(p, _quads(rt, qc, inst.n_p, inst.n_phi), 2, rt.RT_HEUN, 0.5 * p.mesh.dx))
@@ -411,7 +418,8 @@ def run_sweep(args, w):
     from paper_2505_17284_gb300 import sweep as S
     B.build()
     rt.load_library()
-    jobs = sweep_jobs(rt, w["k"], w["grids"])
+    dp = w.get("dp", 1)
+    jobs = sweep_jobs(rt, w["k"], w["grids"], dp=dp)
     # autotuned tiles: one rt_autotune per distinct shape for the one-at-a-time
     # path, and the batch-level segment length for the batched path
     shapes = {}
@@ -435,9 +443,12 @@ def run_sweep(args, w):
     out = {
         "metric": "batched solves/s", "value": k / tb, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded lattice DP-1 sweep)",
+        "data": f"synthetic (seeded lattice DP-{dp} sweep)",
         "config": {"workload": args.workload, "instances": k, "grids": list(w["grids"]), "ordinates": [64, 128, 256],
-                   "sigma_a": "U[5,15]", "sigma_s": "U[0.5,1.5]", "scheme": "MUSCL Heun", "psi_storage": "fp32",
+                   **({"sigma_a": "U[5,15]", "sigma_s": "U[0.5,1.5]"} if dp == 1 else
+                      {"sigma_a_ij": "blue blocks U[5,15], others U[0,0.5]",
+                       "sigma_s_ij": "blue blocks U[0,0.5], others U[0.5,1.5]", "materials": 49}),
+                   "scheme": "MUSCL Heun", "psi_storage": "fp32",
                    "step": "one whole sweep (all instances to their N_t = 0.914 n)",
                    "batch_tile_y": best_ty, "batch_tile_y_ms_per_step": ty_times,
                    "plain_tiles": "rt_autotune per shape", "l2": "working set of the large-grid instances > L2"},

@@ -57,7 +57,7 @@ enum { RT_EULER = 0, RT_HEUN = 1 };
 enum { RT_FP32 = 0, RT_BF16 = 1 };
 enum { RT_SIDE_XMIN = 0, RT_SIDE_XMAX = 1, RT_SIDE_YMIN = 2, RT_SIDE_YMAX = 3 };
 
-#define RT_MAX_MATERIALS 16
+#define RT_MAX_MATERIALS 64
 #define RT_MAX_REGIONS 16
 
 /* Spatial mesh (Sec. 4.2).
@@ -80,7 +80,9 @@ typedef struct {
 
 /* Piecewise-constant materials (Sec. 3.1, 3.2): per material sigma_a, sigma_s
  * (sigma_t = sigma_a + sigma_s) and isotropic source Q; per cell a material id
- * (0..n_mat-1) and a QoI region id (0..n_regions-1). n_mat, n_regions <= 16. */
+ * (0..n_mat-1) and a QoI region id (0..n_regions-1). n_mat <= RT_MAX_MATERIALS
+ * (64: one material per block of the 7 x 7 lattice, the per-block parameters
+ * of Sec. 3.1.3, fits), n_regions <= RT_MAX_REGIONS. */
 typedef struct {
   int32_t n_mat;
   const double* sigma_a;
@@ -383,7 +385,7 @@ void rt_batch_destroy(rt_batch* b);
  *   RT_STAGE_EULER / RT_STAGE_HEUN1 (psi_out = psi_in + dt F(psi_in)) or
  *   RT_STAGE_HEUN2 (psi_out = (psi_n + psi_in + dt F(psi_in))/2; psi_out may be
  *   psi_n); storage RT_FP32 or RT_BF16; tile_y rows per work item (0 = default);
- *   material table on the host (n_mat <= 16, n_regions <= 16); inflow psi^- per
+ *   material table on the host (n_mat <= 64, n_regions <= 16); inflow psi^- per
  *   side (x-, x+, y-, y+; 0 = vacuum); dt; psi_in, psi_n, psi_out (16-byte
  *   aligned, psi_out distinct from psi_in); phi_in = sum_k w_k psi_in,k and
  *   phi_out (float [cell]); cell_mat, cell_region (uint8 [cell]); xi, eta, w

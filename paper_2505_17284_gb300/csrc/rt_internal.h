@@ -15,7 +15,7 @@
 
 namespace rtk {
 
-constexpr int kMaxMat = 16;
+constexpr int kMaxMat = 64;
 constexpr int kMaxReg = 16;
 constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow

@@ -88,13 +88,15 @@ class rt_problem(C.Structure):
 
 RT_STAGE_EULER, RT_STAGE_HEUN1, RT_STAGE_HEUN2 = 0, 1, 2
 RT_NOALLOC_MAX_WORK_ITEMS = 8192
+RT_MAX_MATERIALS = 64
 
 
 class rt_cart_stage_args(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double), ("dy", C.c_double),
                 ("M_pad", C.c_int32), ("vec", C.c_int32), ("order", C.c_int32), ("stage", C.c_int32),
                 ("storage", C.c_int32), ("tile_y", C.c_int32), ("n_mat", C.c_int32), ("n_regions", C.c_int32),
-                ("sigma_a", C.c_double * 16), ("sigma_s", C.c_double * 16), ("Q", C.c_double * 16),
+                ("sigma_a", C.c_double * RT_MAX_MATERIALS), ("sigma_s", C.c_double * RT_MAX_MATERIALS),
+                ("Q", C.c_double * RT_MAX_MATERIALS),
                 ("inflow", C.c_double * 4), ("dt", C.c_double),
                 ("psi_in", C.c_void_p), ("psi_n", C.c_void_p), ("psi_out", C.c_void_p),
                 ("phi_in", C.c_void_p), ("phi_out", C.c_void_p), ("cell_mat", C.c_void_p),

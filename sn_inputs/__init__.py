@@ -169,6 +169,38 @@ def lattice_problem(n: int, sigma_a_blue=10.0, sigma_s_scatter=1.0, t_end=3.2) -
     return Problem(mesh=mesh, materials=m, boundary=Boundary(), t_end=t_end, name=f"lattice{n}")
 
 
+def lattice_dp2_nominal():
+    """Per-block cross-sections [7, 7] (index [i, j], i along x) equal to the
+    nominal table of Sec. 3.1: the DP-2 point at which the lattice is the
+    three-material checkerboard."""
+    bi, bj = np.meshgrid(np.arange(7), np.arange(7), indexing="ij")
+    cls = lattice_block_material(bi, bj)
+    sa, ss, _ = lattice_materials_table()
+    return sa[cls], ss[cls]
+
+
+def lattice_dp2_problem(n: int, sigma_a_blocks, sigma_s_blocks, q_red=1.0, t_end=3.2) -> Problem:
+    """Lattice with the DP-2 design parameters of Sec. 3.1.3: one absorption and
+    one scattering cross-section per block C_ij (arrays [7, 7], index [i, j], i
+    along x). Material id = 7 j + i (49 materials); the source Q = q_red sits in
+    the red centre block only; the QoI regions stay the white / blue / red
+    classes of the nominal layout."""
+    sa = np.asarray(sigma_a_blocks, dtype=np.float64)
+    ss = np.asarray(sigma_s_blocks, dtype=np.float64)
+    assert sa.shape == (7, 7) and ss.shape == (7, 7)
+    mesh = CartesianMesh(nx=n, ny=n, x0=0.0, y0=0.0, dx=7.0 / n, dy=7.0 / n)
+    xc, yc = mesh.centres()
+    bi, bj = np.floor(xc).astype(int), np.floor(yc).astype(int)
+    mat = (7 * bj + bi).astype(np.int32)
+    region = lattice_block_material(bi, bj)
+    # material m = 7 j + i: flatten [i, j] with j slowest
+    Q = np.zeros(49)
+    Q[7 * LATTICE_SOURCE[1] + LATTICE_SOURCE[0]] = q_red
+    m = Materials(sigma_a=sa.T.ravel().copy(), sigma_s=ss.T.ravel().copy(), Q=Q, cell_mat=mat,
+                  cell_region=region, region_names=LATTICE_REGIONS)
+    return Problem(mesh=mesh, materials=m, boundary=Boundary(), t_end=t_end, name=f"lattice{n}_dp2")
+
+
 def lattice_triangle_problem(n: int, jitter=0.0, seed=0, t_end=3.2) -> Problem:
     """Lattice geometry on the split-square triangle mesh (material by centroid)."""
     mesh = split_grid_mesh(n, 7.0, jitter=jitter, seed=seed)
@@ -335,6 +367,43 @@ def sweep_instances(k: int, seed: int = 0, grids=(70, 140, 280, 560), Ms=(64, 12
         ss = ss_range[0] + (ss_range[1] - ss_range[0]) * u[3]
         n_p, n_phi = QUAD_SHAPES[M]
         out.append(SweepInstance(n=n, n_p=n_p, n_phi=n_phi, sigma_a=float(sa), sigma_s=float(ss)))
+    return out
+
+
+@dataclass
+class Dp2Instance:
+    n: int
+    n_p: int
+    n_phi: int
+    sigma_a: np.ndarray          # [7, 7]
+    sigma_s: np.ndarray          # [7, 7]
+
+    @property
+    def M(self) -> int:
+        return self.n_p * self.n_phi
+
+
+def dp2_instances(k: int, seed: int = 0, grids=(70, 140, 280, 560), Ms=(64, 128, 256),
+                  blue_sa=(5.0, 15.0), blue_ss=(0.0, 0.5), other_sa=(0.0, 0.5), other_ss=(0.5, 1.5)) -> list:
+    """Lattice DP-2 parameter sweep (Sec. 3.1.3): instance i takes draws
+    100 i .. 100 i + 99 of the splitmix64 stream `seed`: grid, ordinate count,
+    then 49 absorption and 49 scattering cross-sections, block by block (i
+    along x fastest). Blocks of the nominal blue set draw from the strong
+    absorber ranges, all others from the scatterer ranges, so that every draw
+    keeps the lattice's character while all 98 parameters vary."""
+    bi, bj = np.meshgrid(np.arange(7), np.arange(7), indexing="ij")
+    blue = lattice_block_material(bi, bj) == MAT_BLUE        # [i, j]
+    out = []
+    for t in range(k):
+        u = uniform01(seed, np.arange(100 * t, 100 * t + 100, dtype=np.uint64))
+        n = grids[min(int(u[0] * len(grids)), len(grids) - 1)]
+        M = Ms[min(int(u[1] * len(Ms)), len(Ms) - 1)]
+        ua = u[2:51].reshape(7, 7).T          # [i, j] from the order j slowest
+        us = u[51:100].reshape(7, 7).T
+        sa = np.where(blue, blue_sa[0] + (blue_sa[1] - blue_sa[0]) * ua, other_sa[0] + (other_sa[1] - other_sa[0]) * ua)
+        ss = np.where(blue, blue_ss[0] + (blue_ss[1] - blue_ss[0]) * us, other_ss[0] + (other_ss[1] - other_ss[0]) * us)
+        n_p, n_phi = QUAD_SHAPES[M]
+        out.append(Dp2Instance(n=n, n_p=n_p, n_phi=n_phi, sigma_a=sa, sigma_s=ss))
     return out
 
 

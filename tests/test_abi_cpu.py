@@ -87,7 +87,7 @@ def _create(rt, problem, quad, **kw):
     ({"mesh.dx": -1.0}, {}),
     ({"mesh.kind": 7}, {}),
     ({"mat.n_mat": 0}, {}),
-    ({"mat.n_mat": 17}, {}),
+    ({"mat.n_mat": 65}, {}),
     ({"mat.n_regions": 0}, {}),
     ({"q.M": 0}, {}),
     ({"bc.side_kind": 2}, {}),        # periodic: not on the GPU path

@@ -208,6 +208,53 @@ def test_muscl_heun_lattice_mass_balance_and_symmetry(rt):
     assert np.max(np.abs(ph - ph[:, ::-1])) <= 1e-5 * ph.max()
 
 
+# ------------------------------------------------------------------ DP-2: per-block cross-sections
+@pytest.mark.parametrize("integrator", ["euler", "heun"])
+def test_lattice_dp2_per_block_parameters(rt, integrator):
+    """DP-2 (Sec. 3.1.3): 49 block materials with drawn sigma_a, sigma_s, on an
+    84^2 grid (ragged tiles) from a random state, so every block's
+    cross-sections enter the first step; MUSCL, 4x32 ordinates."""
+    d = si.dp2_instances(1, seed=11)[0]
+    p = si.lattice_dp2_problem(84, d.sigma_a, d.sigma_s)
+    integ = rt.RT_EULER if integrator == "euler" else rt.RT_HEUN
+    psi0 = si.random_psi(p.mesh.n_cells, 128, seed=5)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 32, 2, integ, 10, psi0=psi0, dt=0.5 * p.mesh.dx,
+                                                  tile_y=24)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_lattice_dp2_nominal_equals_three_materials_bitwise(rt):
+    """The nominal DP-2 point (49 materials carrying the three-material values)
+    gives the checkerboard's result to the bit: material lookup is exact."""
+    sa, ss = si.lattice_dp2_nominal()
+    outs = []
+    for p in (si.lattice_dp2_problem(70, sa, ss, t_end=1.0), si.lattice_problem(70, t_end=1.0)):
+        s = rt.Solver(p, rt.rt_quad_product(4, 16), order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+        s.step()
+        outs.append((s.psi(), s.qoi()))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in ("mass", "abs_int", "outflow_int"):
+        assert np.array_equal(np.asarray(outs[0][1][k]), np.asarray(outs[1][1][k])), k
+
+
+def test_dp2_materials_on_triangles(rt):
+    """Per-block materials (49 ids) through the triangle kernel's packed
+    material/region word, against the oracle."""
+    d = si.dp2_instances(1, seed=12)[0]
+    t = si.lattice_triangle_problem(21, jitter=0.2, seed=3, t_end=0.5)
+    xc, yc = t.mesh.centroids()
+    bi, bj = np.floor(xc).astype(int), np.floor(yc).astype(int)
+    t.materials = si.Materials(sigma_a=d.sigma_a.T.ravel().copy(), sigma_s=d.sigma_s.T.ravel().copy(),
+                               Q=np.where(np.arange(49) == 24, 1.0, 0.0), cell_mat=(7 * bj + bi).astype(np.int32),
+                               cell_region=si.lattice_block_material(bi, bj), region_names=si.LATTICE_REGIONS)
+    psi0 = si.random_psi(t.mesh.n_cells, 64, seed=6)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, t, 4, 16, 1, rt.RT_HEUN, 6, psi0=psi0)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
 # ------------------------------------------------------------------ triangles
 @pytest.mark.parametrize("integrator", ["euler", "heun"])
 def test_enclosure_triangles(rt, integrator):

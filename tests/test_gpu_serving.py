@@ -43,6 +43,31 @@ def test_sweep_batched_equals_one_at_a_time(rt):
     assert best in times and all(t > 0 for t in times.values())
 
 
+def test_dp2_sweep_batched_equals_one_at_a_time_and_the_oracle(rt):
+    """A DP-2 sweep (49 block materials per instance) through the batched
+    path: each result equals the instance solved alone, and a small one
+    matches the FP64 oracle."""
+    from paper_2505_17284_gb300 import sweep as S
+    from paper_2505_17284_gb300.sweep import Job
+    jobs = []
+    for d in si.dp2_instances(5, seed=8, grids=(21, 28, 35), Ms=(64, 128)):
+        p = si.lattice_dp2_problem(d.n, d.sigma_a, d.sigma_s, t_end=0.8)
+        jobs.append(Job(p, rt.rt_quad_product(d.n_p, d.n_phi), 2, rt.RT_HEUN, 0.5 * p.mesh.dx))
+    qb, tb, nb = S.solve_batched(jobs)
+    qp, tp, per, npl = S.solve_plain(jobs, tune=False)
+    assert nb == npl
+    for a, b in zip(qb, qp):
+        for k in a:
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+    j = min(jobs, key=lambda j: j.n_cells * j.M)
+    d = si.dp2_instances(5, seed=8, grids=(21, 28, 35), Ms=(64, 128))[jobs.index(j)]
+    op = oracle.CartesianOracle(j.problem, oracle.product_quadrature(d.n_p, d.n_phi), order=2)
+    n = qb[jobs.index(j)]["n_steps"]
+    _, acc, Sn = oracle.run(op, np.zeros((j.n_cells, j.M)), j.dt, n, "heun")
+    assert S.qoi_rel_diff(qb[jobs.index(j)], {"mass": Sn["mass"], "abs_int": acc.abs_int,
+                                              "outflow_int": acc.outflow_int}) <= 1e-4
+
+
 def stream(rt, kinds):
     from paper_2505_17284_gb300.serve import Request, estimate_bytes
     from paper_2505_17284_gb300.sweep import Job

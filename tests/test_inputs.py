@@ -68,3 +68,49 @@ def test_sweep_draws():
     assert inst[3].n == si.sweep_instances(4, seed=0)[3].n
     t = si.poisson_arrivals(2000, rate=10.0, seed=0)
     assert np.all(np.diff(t) > 0) and abs(t[-1] / 2000 - 0.1) < 0.01
+
+
+def test_dp2_nominal_is_the_lattice():
+    """At the nominal per-block values the DP-2 lattice (49 materials, Sec.
+    3.1.3) gives every cell the cross-sections and source of the three-material
+    checkerboard, and the oracle's solution is the same to the bit."""
+    import oracle
+    sa, ss = si.lattice_dp2_nominal()
+    assert sa.shape == (7, 7) and sa[1, 1] == 10.0 and ss[1, 1] == 0.0 and ss[0, 0] == 1.0
+    p, q = si.lattice_dp2_problem(14, sa, ss, t_end=0.4), si.lattice_problem(14, t_end=0.4)
+    P, Q = p.materials, q.materials
+    assert len(P.sigma_a) == 49 and P.cell_mat.max() == 48
+    for f in ("sigma_a", "sigma_s", "Q"):
+        assert np.array_equal(getattr(P, f)[P.cell_mat], getattr(Q, f)[Q.cell_mat]), f
+    assert np.array_equal(P.cell_region, Q.cell_region)
+    # material id is the block index 7 j + i of the cell's block
+    xc, yc = p.mesh.centres()
+    assert np.array_equal(P.cell_mat, 7 * np.floor(yc).astype(int) + np.floor(xc).astype(int))
+    quad = oracle.product_quadrature(2, 8)
+    outs = []
+    for pr in (p, q):
+        op = oracle.CartesianOracle(pr, quad, order=2)
+        outs.append(oracle.run(op, np.zeros((pr.mesh.n_cells, 16)), 0.25, 8, "heun"))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1].abs_int, outs[1][1].abs_int)
+
+
+def test_dp2_draws():
+    inst = si.dp2_instances(64, seed=3)
+    bi, bj = np.meshgrid(np.arange(7), np.arange(7), indexing="ij")
+    blue = si.lattice_block_material(bi, bj) == si.MAT_BLUE
+    assert blue.sum() == 11
+    for d in inst:
+        assert d.sigma_a.shape == (7, 7) and d.sigma_s.shape == (7, 7)
+        assert np.all((d.sigma_a[blue] >= 5) & (d.sigma_a[blue] <= 15))
+        assert np.all((d.sigma_s[blue] >= 0) & (d.sigma_s[blue] <= 0.5))
+        assert np.all((d.sigma_a[~blue] >= 0) & (d.sigma_a[~blue] <= 0.5))
+        assert np.all((d.sigma_s[~blue] >= 0.5) & (d.sigma_s[~blue] <= 1.5))
+        assert len(np.unique(d.sigma_a)) == 49 and len(np.unique(d.sigma_s)) == 49
+    assert {d.n for d in inst} == {70, 140, 280, 560} and {d.M for d in inst} == {64, 128, 256}
+    again = si.dp2_instances(8, seed=3)
+    assert all(np.array_equal(a.sigma_a, b.sigma_a) and a.n == b.n for a, b in zip(inst[:8], again))
+    # draw order: block (i, j) takes draw 2 + 7 j + i of its instance
+    u = si.uniform01(3, np.arange(100, 200, dtype=np.uint64))
+    assert inst[1].sigma_a[2, 0] == 0.5 * u[2 + 2]
+    assert inst[1].sigma_a[1, 1] == 5.0 + 10.0 * u[2 + 7 + 1]
