@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "S_N cell-ordinate updates/s"
 UNIT = "updates/s"
+QOI_BYTES = 392   # sizeof(rt_qoi_t): the QoI read-back of one problem
 
 WORKLOADS = {
     # name: (mesh, n, n_p, n_phi, order, integrator, storage, dt_factor, t_end); n_p = 0 selects the
@@ -255,7 +256,8 @@ def run_ours(args, spec):
     updates = dof * K * world
     value = updates / (ms * 1e-3)
     bpu = bytes_per_update(order, integ, storage)
-    launches_per_step = info.stages_per_step
+    # each stage launch is followed by the QoI-box launch when the problem has boxes
+    launches_per_step = info.stages_per_step * (2 if info.n_box_items else 1)
     achieved_gbs = dof * bpu * K / (ms * 1e-3) / 1e9
     peaks = {}
     try:
@@ -280,10 +282,13 @@ def run_ours(args, spec):
     e2e_s = time.perf_counter() - t0
     n_cells = info.n_cells
     if mesh == "lattice":
-        h2d = 2 * n_cells + 3 * info.M_pad * 4
+        # per-cell material and region bytes, the quadrature, 16 bytes per QoI-box face
+        n_faces = sum(2 * round((b[1] - b[0]) / problem.mesh.dx) + 2 * round((b[3] - b[2]) / problem.mesh.dy)
+                      for b in problem.extra.get("boxes", ()))
+        h2d = 2 * n_cells + 3 * info.M_pad * 4 + 16 * n_faces
     else:
         h2d = n_cells * (16 + 32) + 3 * info.M_pad * 4
-    d2h = 336
+    d2h = QOI_BYTES
 
     tb, traffic_src = profiled_traffic(args.workload, "cart" if mesh == "lattice" else "tri")
     traffic = tb * dof if tb is not None else None
@@ -312,7 +317,8 @@ def run_ours(args, spec):
         "gpu_launches": K * launches_per_step,
         "clocks": clk,
         "qoi_after": {"step": q["step"], "abs_int_blue": float(q["abs_int"][1]) if mesh == "lattice" else None,
-                      "mass": q["mass"]},
+                      "mass": q["mass"], "box_out_now": [float(v) for v in q["box_out_now"]],
+                      "box_out_int": [float(v) for v in q["box_out_int"]]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, secs = oracle_sample(spec, budget_s=args.cpu_budget)
@@ -463,7 +469,7 @@ def run_sweep(args, w):
         "roofline": {"bound": "hbm", "achieved": nbytes / tb / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": nbytes / tb / 1e9 / peak, "traffic": None, "kernel": "cart_stage_kernel (batched)",
                      "peak_source": peak_src},
-        "e2e": {"value": k / tb, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": k * 336,
+        "e2e": {"value": k / tb, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": k * QOI_BYTES,
                 "includes": "batch creation from host arrays, all steps, QoI read-back, destroy"},
         "gpu_launches": {"batched": 2 * max(steps_b) * len({j.M for j in jobs}) + k,
                          "plain": sum(2 * n + 1 for n in steps_p),
@@ -551,7 +557,7 @@ def run_serve(args, w):
         "qoi_rel_diff": {"bf16_vs_fp32_max": max(d_bf16), "bf16_vs_fp32_median": float(np.median(d_bf16)),
                          "served_fp32_vs_alone_max": max(d_plain)},
         "e2e": {"value": count / out32["span"], "unit": "solves/s", "h2d_bytes_per_step": None,
-                "d2h_bytes_per_step": count * 336, "includes": "problem build on the host, admission, all steps, "
+                "d2h_bytes_per_step": count * QOI_BYTES, "includes": "problem build on the host, admission, all steps, "
                                                                "QoI read-back, removal"},
         "gpu_launches": None,
         "clocks": clk,

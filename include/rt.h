@@ -59,6 +59,7 @@ enum { RT_SIDE_XMIN = 0, RT_SIDE_XMAX = 1, RT_SIDE_YMIN = 2, RT_SIDE_YMAX = 3 };
 
 #define RT_MAX_MATERIALS 64
 #define RT_MAX_REGIONS 16
+#define RT_MAX_BOXES 4
 
 /* Spatial mesh (Sec. 4.2).
  *   kind = RT_MESH_CARTESIAN: nx x ny rectangles of size dx x dy with lower-left
@@ -91,6 +92,15 @@ typedef struct {
   const int32_t* cell_mat;
   const int32_t* cell_region;
   int32_t n_regions;
+  /* QoI boxes (Sec. 3.1 QoI-1/2: the squares S_l, l in {1.5, 2.5}, of the
+   * lattice): n_boxes (0..RT_MAX_BOXES) axis-aligned rectangles
+   * boxes[4 b + {0,1,2,3}] = {x_lo, x_hi, y_lo, y_hi}. Cartesian meshes only.
+   * Every edge must lie on a grid line (within 1e-9 relative) strictly inside
+   * the domain, so that each face of a box has a cell on both sides. For each
+   * box the library reports the particle flow leaving it (rt_qoi_t.box_out_*).
+   * n_boxes = 0 (boxes may be NULL): none. */
+  int32_t n_boxes;
+  const double* boxes;
 } rt_materials;
 
 /* Ordinates on the upper hemisphere (Sec. 4.1): direction components xi_k,
@@ -170,6 +180,17 @@ typedef struct {
   double outflow_now;
   double outflow_int;
   double source_int;
+  /* QoI boxes (rt_materials.boxes), b < n_boxes:
+   *   box_out_now[b] = sum over the faces f of the box's boundary of
+   *     l_f sum_k w_k max(omega_k . n_f, 0) psi_hat_k,f at time t, n_f the
+   *     normal pointing out of the box and psi_hat the scheme's upwind trace
+   *     (for a leaving ordinate, the inside cell's value at first order, its
+   *     MUSCL-minmod reconstruction at second order): Sec. 3.1 QoI-1;
+   *   box_out_int[b] = its time integral with the scheme's weights: QoI-2. */
+  int32_t n_boxes;
+  int32_t pad;
+  double box_out_now[RT_MAX_BOXES];
+  double box_out_int[RT_MAX_BOXES];
 } rt_qoi_t;
 
 /* Static facts about a solver. */
@@ -190,7 +211,8 @@ typedef struct {
                         caller's order does not give sign-uniform chunks and the padding adds at most
                         1/8; M_pad is then the padded count). rt_get_psi / rt_set_psi always use the
                         caller's order; rt_device_state exposes the internal one. */
-  int32_t pad;
+  int32_t n_box_items; /* QoI boxes: work items of the box-outflow launch that follows each stage
+                          (0: no boxes, no such launch) */
 } rt_info_t;
 
 typedef struct rt_solver rt_solver;
@@ -229,7 +251,7 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
  * enqueueing. Each step is one launch (Euler) or two (Heun stages). */
 rt_status rt_step(rt_solver* s, int64_t n);
 
-/* Synchronise the stream and copy the QoIs to *out (about 300 bytes). Returns
+/* Synchronise the stream and copy the QoIs to *out (392 bytes). Returns
  * RT_ETIMEOUT / RT_ENONFINITE (and enters the error state) if a kernel
  * reported one. */
 rt_status rt_qoi(rt_solver* s, rt_qoi_t* out);

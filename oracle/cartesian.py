@@ -23,6 +23,13 @@ QoI integrands of a state (Sec. 3.1 QoI-3..5 and the mass balance):
   abs[r]  = sum_{i in region r} A_i sigma_a,i phi_i
   mass    = sum_i A_i phi_i
   outflow = sum_{boundary faces} l sum_k w_k (omega_k . n) psi_hat_k
+and, for each QoI box b (problem.extra["boxes"], rectangles (x_lo, x_hi, y_lo,
+y_hi) with edges on grid lines; the squares S_l of Sec. 3.1 QoI-1/2):
+  box_out[b] = sum_{faces f of the box boundary} l_f sum_k w_k max(omega_k . n_f, 0) psi_hat_k,f
+with n_f pointing out of the box and psi_hat the same upwind trace the fluxes
+use, i.e. the outflow through the box boundary of Sec. 3.1 QoI-1 evaluated with
+the scheme's own traces (reading: the paper defines the integral for the
+continuous solution and leaves the discrete trace open).
 """
 import numpy as np
 
@@ -64,6 +71,17 @@ class CartesianOracle:
             on = normals[s][0] * self.xi + normals[s][1] * self.eta
             val = bc.inflow[s] if self.kind[s] == INFLOW else 0.0
             self.ghost.append(np.where(on < 0.0, val, 0.0))
+        # QoI boxes as cell index ranges [i0, i1) x [j0, j1)
+        self.boxes = []
+        for box in problem.extra.get("boxes", ()):
+            lim = []
+            for e, v in enumerate(box):
+                o, h = (mesh.x0, mesh.dx) if e < 2 else (mesh.y0, mesh.dy)
+                r = int(round((v - o) / h))
+                if abs(o + r * h - v) > 1e-9 * max(1.0, abs(v)):
+                    raise ValueError(f"box edge {v} is not a grid line")
+                lim.append(r)
+            self.boxes.append(tuple(lim))
 
     # ------------------------------------------------------------------
     def phi(self, psi):
@@ -153,12 +171,34 @@ class CartesianOracle:
             tot += self.dx * np.sum((Ty[self.ny, :, :] * self.eta) @ self.w)
         return float(tot)
 
+    def box_flow(self, psi):
+        """(out, in) per QoI box: particle flow leaving and entering through the
+        box boundary, sum over its faces of l sum_k w_k max(+-omega_k . n, 0)
+        psi_hat_k with the upwind traces of the fluxes (n out of the box)."""
+        Tx, Ty = self.traces(psi)
+        fx, fy = Tx.shape[1], Ty.shape[0]       # faces per row / column (nx+1 bounded, nx periodic)
+        out, inn = [], []
+        for (i0, i1, j0, j1) in self.boxes:
+            sides = ((Tx[j0:j1, i0 % fx, :], -self.xi, self.dy), (Tx[j0:j1, i1 % fx, :], self.xi, self.dy),
+                     (Ty[j0 % fy, i0:i1, :], -self.eta, self.dx), (Ty[j1 % fy, i0:i1, :], self.eta, self.dx))
+            o = n = 0.0
+            for T, on, l in sides:
+                o += l * float(np.sum(T @ (self.w * np.maximum(on, 0.0))))
+                n += l * float(np.sum(T @ (self.w * np.maximum(-on, 0.0))))
+            out.append(o)
+            inn.append(n)
+        return np.array(out), np.array(inn)
+
     def integrands(self, psi):
-        """QoI integrands at state psi: abs per region, mass, outflow."""
+        """QoI integrands at state psi: abs per region, mass, outflow (and the
+        outflow of each QoI box, if any)."""
         phi = self.phi(psi)
         a = self.area * self.sigma_a * phi
         absr = np.array([a[self.region == r].sum() for r in range(self.n_regions)])
-        return {"abs": absr, "mass": float(self.area * phi.sum()), "outflow": self.outflow(psi)}
+        S = {"abs": absr, "mass": float(self.area * phi.sum()), "outflow": self.outflow(psi)}
+        if self.boxes:
+            S["box_out"] = self.box_flow(psi)[0]
+        return S
 
     def source_rate(self):
         """Particles emitted per unit time: sum_i A_i Q_i sum_k w_k = 2 pi sum_i A_i Q_i."""

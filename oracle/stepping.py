@@ -7,7 +7,8 @@ Forward Euler: psi^{n+1} = psi^n + dt F(psi^n) (the first-order "plain" method).
 The time-integrated QoIs (Sec. 3.1 QoI-2/QoI-4, Sec. 3.2 QoI-2) use the
 weights of the scheme itself, so that the discrete mass balance is an exact
 identity: Euler adds dt*S(psi^n), Heun adds dt/2*(S(psi^n) + S(psi1)), where
-S(psi) are the integrands (absorption per region, outflow) at a state.
+S(psi) are the integrands (absorption per region, outflow, box outflow) at a
+state.
 """
 import math
 
@@ -40,12 +41,17 @@ class Accumulators:
     def __init__(self, n_regions):
         self.abs_int = np.zeros(n_regions)
         self.outflow_int = 0.0
+        self.box_out_int = None      # per QoI box, once a state with boxes is added
         self.t = 0.0
         self.step = 0
 
     def add(self, weight, S):
         self.abs_int += weight * S["abs"]
         self.outflow_int += weight * S["outflow"]
+        if "box_out" in S:
+            if self.box_out_int is None:
+                self.box_out_int = np.zeros_like(S["box_out"])
+            self.box_out_int += weight * S["box_out"]
 
 
 def run(op, psi0, dt, n_steps, integrator="euler", acc=None):

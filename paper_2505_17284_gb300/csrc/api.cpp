@@ -21,6 +21,7 @@ struct rt_solver {
   InstDesc* d_desc = nullptr;
   WorkItem* d_stage_items = nullptr;
   WorkItem* d_init_items = nullptr;
+  WorkItem* d_box_items = nullptr;     // QoI boxes (none: nullptr)
   int64_t host_step = 0;               // steps enqueued
   bool failed = false;
   cudaGraphExec_t graph = nullptr;
@@ -40,7 +41,8 @@ rt_status launch_steps_direct(rt_solver* s, int64_t n, cudaStream_t stream) {
   const Instance& I = s->I;
   for (int64_t i = 0; i < n; ++i) {
     rt_status st = launch_step(s->d_desc, s->d_stage_items, (int)I.stage_items.size(), I.kind, I.integrator,
-                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream, I.uni);
+                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream, I.uni, s->d_box_items,
+                               (int)I.box_items.size());
     if (st != RT_OK) return st;
   }
   return RT_OK;
@@ -76,12 +78,8 @@ rt_status read_state(rt_solver* s, InstState* h) { return read_inst_state(s->I, 
 
 rt_status run_init(rt_solver* s) {
   const Instance& I = s->I;
-  cudaError_t e = launch_init(s->d_desc, s->d_init_items, (int)I.init_items.size(), I.vec, I.storage, s->stream);
-  if (e != cudaSuccess) {
-    set_error("init launch failed: %s", cudaGetErrorString(e));
-    return RT_ECUDA;
-  }
-  return RT_OK;
+  return launch_init_all(s->d_desc, s->d_init_items, (int)I.init_items.size(), s->d_box_items,
+                         (int)I.box_items.size(), I.vec, I.storage, s->stream);
 }
 
 size_t elem_size(const Instance& I) { return I.storage == RT_BF16 ? 2 : 4; }
@@ -124,12 +122,18 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
   s->d_stage_items = (WorkItem*)p;
   if ((st = s->arena.get(I.init_items.size() * sizeof(WorkItem), &p)) != RT_OK) return bail(st);
   s->d_init_items = (WorkItem*)p;
+  if (!I.box_items.empty()) {
+    if ((st = s->arena.get(I.box_items.size() * sizeof(WorkItem), &p)) != RT_OK) return bail(st);
+    s->d_box_items = (WorkItem*)p;
+  }
   I.device_bytes = s->arena.bytes;
   if (cudaMemcpyAsync(s->d_desc, &I.desc, sizeof(InstDesc), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemcpyAsync(s->d_stage_items, I.stage_items.data(), I.stage_items.size() * sizeof(WorkItem),
                       cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemcpyAsync(s->d_init_items, I.init_items.data(), I.init_items.size() * sizeof(WorkItem),
-                      cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+                      cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      (s->d_box_items && cudaMemcpyAsync(s->d_box_items, I.box_items.data(), I.box_items.size() * sizeof(WorkItem),
+                                         cudaMemcpyHostToDevice, s->stream) != cudaSuccess)) {
     set_error("copying the solver descriptor failed: %s", cudaGetErrorString(cudaGetLastError()));
     return bail(RT_ECUDA);
   }
@@ -201,6 +205,7 @@ rt_status rt_info(const rt_solver* s, rt_info_t* out) {
   out->variant = I.kind == RT_MESH_CARTESIAN ? (I.uni ? 2 : 1) : 0;
   out->vec = I.kind == RT_MESH_CARTESIAN ? I.cvec : I.vec;
   out->regrouped = I.regrouped;
+  out->n_box_items = (int32_t)I.box_items.size();
   return RT_OK;
 }
 

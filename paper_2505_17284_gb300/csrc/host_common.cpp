@@ -405,6 +405,44 @@ static void cell_range_items(int64_t n_cells, std::vector<WorkItem>& items) {
   }
 }
 
+// ---------------------------------------------------------------- QoI boxes
+// Face records of the QoI boxes (Sec. 3.1 QoI-1/2) on a Cartesian grid: for each
+// box, its x- side (inside column i_lo, rows j_lo..j_hi-1), x+ side (column
+// i_hi-1), y- side (row j_lo, columns i_lo..i_hi-1) and y+ side (row j_hi-1), in
+// that order; per face {inside cell, outside cell, the inside cell's other
+// neighbour along the normal, box | side << 8}.
+static rt_status build_box_faces(const rt_mesh* mesh, const rt_materials* mat, std::vector<int4>& faces) {
+  faces.clear();
+  if (mat->n_boxes == 0) return RT_OK;
+  if (mat->n_boxes < 0 || mat->n_boxes > RT_MAX_BOXES) { set_error("n_boxes must be in 0..%d", RT_MAX_BOXES); return RT_EINVAL; }
+  if (!mat->boxes) { set_error("boxes is NULL"); return RT_EINVAL; }
+  if (mesh->kind != RT_MESH_CARTESIAN) { set_error("QoI boxes need a Cartesian mesh"); return RT_EINVAL; }
+  const int nx = mesh->nx;
+  for (int b = 0; b < mat->n_boxes; ++b) {
+    int lim[4];
+    for (int e = 0; e < 4; ++e) {
+      const double v = mat->boxes[4 * b + e];
+      const double o = e < 2 ? mesh->x0 : mesh->y0, h = e < 2 ? mesh->dx : mesh->dy;
+      const int n = e < 2 ? mesh->nx : mesh->ny;
+      if (!std::isfinite(v)) { set_error("box %d: edge %d is not finite", b, e); return RT_EINVAL; }
+      const double r = std::nearbyint((v - o) / h);
+      if (std::fabs(o + r * h - v) > 1e-9 * std::max(1.0, std::fabs(v)) || r < 1 || r > n - 1) {
+        set_error("box %d: edge %g is not a grid line strictly inside the domain", b, v);
+        return RT_EINVAL;
+      }
+      lim[e] = (int)r;
+    }
+    const int i0 = lim[0], i1 = lim[1], j0 = lim[2], j1 = lim[3];
+    if (i1 <= i0 || j1 <= j0) { set_error("box %d: need x_lo < x_hi and y_lo < y_hi", b); return RT_EINVAL; }
+    auto cell = [&](int i, int j) { return (int32_t)((int64_t)j * nx + i); };
+    for (int j = j0; j < j1; ++j) faces.push_back(make_int4(cell(i0, j), cell(i0 - 1, j), cell(i0 + 1, j), b | 0 << 8));
+    for (int j = j0; j < j1; ++j) faces.push_back(make_int4(cell(i1 - 1, j), cell(i1, j), cell(i1 - 2, j), b | 1 << 8));
+    for (int i = i0; i < i1; ++i) faces.push_back(make_int4(cell(i, j0), cell(i, j0 - 1), cell(i, j0 + 1), b | 2 << 8));
+    for (int i = i0; i < i1; ++i) faces.push_back(make_int4(cell(i, j1 - 1), cell(i, j1), cell(i, j1 - 2), b | 3 << 8));
+  }
+  return RT_OK;
+}
+
 // ---------------------------------------------------------------- build
 rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_quadrature* quad,
                          const rt_boundary* bc, int order, int integrator, int storage, double dt_target,
@@ -426,6 +464,8 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   }
   rt_status s = validate_common(mat, quad, bc, order, integrator, storage, t_end, n_cells);
   if (s != RT_OK) return s;
+  std::vector<int4> box_faces;
+  if ((s = build_box_faces(mesh, mat, box_faces)) != RT_OK) return s;
   if (std::isnan(dt_target)) { set_error("dt is not a number"); return RT_EINVAL; }
 
   I.kind = mesh->kind; I.order = order; I.integrator = integrator; I.storage = storage;
@@ -568,6 +608,30 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   const size_t n_part = std::max(I.stage_items.size(), I.init_items.size());
   if ((s = arena.get(n_part * NQ * sizeof(double), &p)) != RT_OK) return s;
   I.partials = (double*)p;
+  // QoI boxes: work items of kBoxFacesPerItem faces
+  I.n_boxes = mat->n_boxes;
+  I.box_items.clear();
+  int4* d_faces = nullptr;
+  double* d_box_part = nullptr;
+  if (!box_faces.empty()) {
+    const int nf = (int)box_faces.size();
+    const int n_it = (nf + kBoxFacesPerItem - 1) / kBoxFacesPerItem;
+    for (int g = 0; g < n_it; ++g) {
+      WorkItem w{};
+      w.inst = 0; w.a = g * kBoxFacesPerItem; w.b = std::min(kBoxFacesPerItem, nf - w.a);
+      w.item = g; w.count = n_it;
+      I.box_items.push_back(w);
+    }
+    keep.emplace_back(box_faces.size() * sizeof(int4));
+    std::memcpy(keep.back().data(), box_faces.data(), box_faces.size() * sizeof(int4));
+    if ((s = arena.get(box_faces.size() * sizeof(int4), &p)) != RT_OK) return s;
+    d_faces = (int4*)p;
+    RT_CUDA_TRY(cudaMemcpyAsync(d_faces, keep.back().data(), box_faces.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                stream));
+    if ((s = arena.get((size_t)n_it * kMaxBox * sizeof(double), &p)) != RT_OK) return s;
+    d_box_part = (double*)p;
+    RT_CUDA_TRY(cudaMemsetAsync(d_box_part, 0, (size_t)n_it * kMaxBox * sizeof(double), stream));
+  }
 
   // host images of per-cell and per-ordinate data (kept alive until the stream syncs)
   keep.emplace_back(3 * (size_t)I.Mpad * sizeof(float));
@@ -673,13 +737,17 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     D.sig_a[m] = sa;
     D.sig_a_f[m] = (float)sa;
   }
+  D.box_faces = d_faces;
+  D.box_partials = d_box_part;
+  D.n_boxes = I.n_boxes;
+  D.n_box_faces = (int32_t)box_faces.size();
   I.device_bytes = arena.bytes;
   return RT_OK;
 }
 
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
                       int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream,
-                      int uni) {
+                      int uni, const WorkItem* d_box_items, int n_box_items) {
   const int stages[2] = {integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
   const int n_st = integrator == RT_HEUN ? 2 : 1;
   for (int i = 0; i < n_st; ++i) {
@@ -692,6 +760,25 @@ rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_ite
       set_error("stage launch failed: %s", cudaGetErrorString(e));
       return RT_ECUDA;
     }
+    if (n_box_items > 0) {
+      e = launch_box_outflow(d_desc, d_box_items, n_box_items, stages[i], storage, stream);
+      if (e != cudaSuccess) {
+        set_error("box outflow launch failed: %s", cudaGetErrorString(e));
+        return RT_ECUDA;
+      }
+    }
+  }
+  return RT_OK;
+}
+
+rt_status launch_init_all(const InstDesc* d_desc, const WorkItem* d_init_items, int n_init_items,
+                          const WorkItem* d_box_items, int n_box_items, int vec, int storage, cudaStream_t stream) {
+  cudaError_t e = launch_init(d_desc, d_init_items, n_init_items, vec, storage, stream);
+  if (e == cudaSuccess && n_box_items > 0)
+    e = launch_box_outflow(d_desc, d_box_items, n_box_items, STAGE_INIT, storage, stream);
+  if (e != cudaSuccess) {
+    set_error("init launch failed: %s", cudaGetErrorString(e));
+    return RT_ECUDA;
   }
   return RT_OK;
 }
@@ -739,6 +826,11 @@ void fill_qoi(const Instance& I, const InstState& h, rt_qoi_t* out) {
   out->outflow_now = h.S_cur[kQOut];
   out->outflow_int = h.I[kQOut];
   out->source_int = out->t * I.source_rate;
+  out->n_boxes = I.n_boxes;
+  for (int b = 0; b < I.n_boxes; ++b) {
+    out->box_out_now[b] = h.B_cur[b];
+    out->box_out_int[b] = h.B_I[b];
+  }
 }
 
 static int64_t convert_chunk(const Instance& I) {

@@ -8,6 +8,8 @@
 //   desc          InstDesc (tensor maps, pointers, constants)
 //   state         InstState (step, buffer parity, status, FP64 QoI sums)
 //   partials      FP64 per-work-item QoI partial sums [n_items][NQ]
+//   box_faces     QoI boxes: one record per face of a box boundary (Cartesian)
+//   box_partials  FP64 per-work-item box outflow partial sums [n_box_items][kMaxBox]
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -17,6 +19,7 @@ namespace rtk {
 
 constexpr int kMaxMat = 64;
 constexpr int kMaxReg = 16;
+constexpr int kMaxBox = 4;             // QoI boxes (outflow through their boundary)
 constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
 constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
@@ -39,6 +42,13 @@ struct InstState {
   double S_cur[NQ];      // integrands at psi^n
   double S_mid[NQ];      // Heun: integrands at psi^(1)
   double I[NQ];          // time integrals (abs, -, outflow)
+  // QoI boxes: outflow through each box boundary, updated by the box kernel
+  uint32_t box_ticket;   // box work items finished in the current launch
+  int32_t pad1;
+  int64_t box_step;      // step at the box kernel's last update (tells a masked stage)
+  double B_cur[kMaxBox]; // at psi^n
+  double B_mid[kMaxBox]; // Heun: at psi^(1)
+  double B_I[kMaxBox];   // time integrals
 };
 
 struct alignas(128) InstDesc {
@@ -77,6 +87,12 @@ struct alignas(128) InstDesc {
   float q_src[kMaxMat];
   float sig_a_f[kMaxMat];       // sigma_a as float (per-cell QoI terms; no FP64 in hot loops)
   double sig_a[kMaxMat];
+  // QoI boxes: face records {inside cell, outside cell, the inside cell's other
+  // neighbour along the normal, box | side << 8} (side 0..3: the box's x-, x+,
+  // y-, y+ side, named by its outward normal)
+  const int4* box_faces;
+  double* box_partials;         // [n_box_items][kMaxBox]
+  int32_t n_boxes, n_box_faces;
 };
 
 struct WorkItem {
@@ -103,6 +119,11 @@ cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, in
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
+// Outflow through the QoI boxes of the state a stage just wrote (stage =
+// STAGE_INIT: the current state), with the stage's time-integration update.
+// Work items: a = first face, b = number of faces.
+cudaError_t launch_box_outflow(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
+                               int storage, cudaStream_t stream);
 // FP64 [cell][M] (caller's ordinate order) <-> storage [cell][Mpad] (internal
 // order); inv: internal slot -> caller ordinate or -1, kmap: caller ordinate ->
 // slot (device arrays; NULL when the orders agree).

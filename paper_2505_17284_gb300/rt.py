@@ -25,6 +25,7 @@ RT_BC_VACUUM, RT_BC_INFLOW, RT_BC_PERIODIC = 0, 1, 2
 RT_EULER, RT_HEUN = 0, 1
 RT_FP32, RT_BF16 = 0, 1
 RT_MAX_REGIONS = 16
+RT_MAX_BOXES = 4
 STATUS_NAMES = {0: "RT_OK", 1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ETIMEOUT",
                 5: "RT_ENONFINITE", 6: "RT_ESTATE"}
 
@@ -40,7 +41,8 @@ class rt_mesh(C.Structure):
 
 class rt_materials(C.Structure):
     _fields_ = [("n_mat", C.c_int32), ("sigma_a", _dp), ("sigma_s", _dp), ("Q", _dp),
-                ("cell_mat", _ip), ("cell_region", _ip), ("n_regions", C.c_int32)]
+                ("cell_mat", _ip), ("cell_region", _ip), ("n_regions", C.c_int32),
+                ("n_boxes", C.c_int32), ("boxes", _dp)]
 
 
 class rt_quadrature(C.Structure):
@@ -68,7 +70,8 @@ class rt_qoi_t(C.Structure):
                 ("n_regions", C.c_int32), ("status", C.c_int32),
                 ("abs_now", C.c_double * RT_MAX_REGIONS), ("abs_int", C.c_double * RT_MAX_REGIONS),
                 ("mass", C.c_double), ("outflow_now", C.c_double), ("outflow_int", C.c_double),
-                ("source_int", C.c_double)]
+                ("source_int", C.c_double), ("n_boxes", C.c_int32), ("pad", C.c_int32),
+                ("box_out_now", C.c_double * RT_MAX_BOXES), ("box_out_int", C.c_double * RT_MAX_BOXES)]
 
 
 class rt_info_t(C.Structure):
@@ -77,7 +80,7 @@ class rt_info_t(C.Structure):
                 ("kind", C.c_int32), ("order", C.c_int32), ("integrator", C.c_int32), ("storage", C.c_int32),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("n_work_items", C.c_int32),
                 ("stages_per_step", C.c_int32), ("device_bytes", C.c_int64), ("variant", C.c_int32),
-                ("vec", C.c_int32), ("regrouped", C.c_int32), ("pad", C.c_int32)]
+                ("vec", C.c_int32), ("regrouped", C.c_int32), ("n_box_items", C.c_int32)]
 
 
 class rt_problem(C.Structure):
@@ -307,6 +310,10 @@ def make_structs(problem, quad, keep: _Keep):
     mat.sigma_a, mat.sigma_s, mat.Q = keep.f64(mt.sigma_a), keep.f64(mt.sigma_s), keep.f64(mt.Q)
     mat.cell_mat, mat.cell_region = keep.i32(mt.cell_mat), keep.i32(mt.cell_region)
     mat.n_regions = max(mt.n_regions, int(np.max(mt.cell_region)) + 1)
+    boxes = np.asarray(problem.extra.get("boxes", ()), dtype=np.float64).reshape(-1, 4)
+    mat.n_boxes = boxes.shape[0]
+    if mat.n_boxes:
+        mat.boxes = keep.f64(boxes.reshape(-1))
     xi, eta, _, w = quad
     q = rt_quadrature()
     q.M = len(xi)
@@ -316,6 +323,15 @@ def make_structs(problem, quad, keep: _Keep):
         bc.side_kind[s] = int(problem.boundary.kind[s])
         bc.inflow[s] = float(problem.boundary.inflow[s])
     return mesh, mat, q, bc
+
+
+def qoi_dict(q: rt_qoi_t, n_regions: int) -> dict:
+    """QoIs as a dict of floats and arrays (box entries of length n_boxes)."""
+    R, B = n_regions, q.n_boxes
+    return {"t": q.t, "step": q.step, "n_steps": q.n_steps, "abs_now": np.array(q.abs_now[:R]),
+            "abs_int": np.array(q.abs_int[:R]), "mass": q.mass, "outflow_now": q.outflow_now,
+            "outflow_int": q.outflow_int, "source_int": q.source_int,
+            "box_out_now": np.array(q.box_out_now[:B]), "box_out_int": np.array(q.box_out_int[:B])}
 
 
 class TorchAllocator:
@@ -406,9 +422,7 @@ class Solver:
     def qoi(self) -> dict:
         q = rt_qoi(self.h)
         R = self.n_regions
-        return {"t": q.t, "step": q.step, "n_steps": q.n_steps, "abs_now": np.array(q.abs_now[:R]),
-                "abs_int": np.array(q.abs_int[:R]), "mass": q.mass, "outflow_now": q.outflow_now,
-                "outflow_int": q.outflow_int, "source_int": q.source_int}
+        return qoi_dict(q, R)
 
     def psi(self) -> np.ndarray:
         return rt_get_psi(self.h, self.n_cells, self.M)
@@ -492,9 +506,7 @@ class Batch:
         q = rt_qoi_t()
         check(_fns().rt_batch_qoi(self.h, i, C.byref(q)))
         R = self.shapes[i][2]
-        return {"t": q.t, "step": q.step, "n_steps": q.n_steps, "abs_now": np.array(q.abs_now[:R]),
-                "abs_int": np.array(q.abs_int[:R]), "mass": q.mass, "outflow_now": q.outflow_now,
-                "outflow_int": q.outflow_int, "source_int": q.source_int}
+        return qoi_dict(q, R)
 
     def psi(self, i) -> np.ndarray:
         n, M, _ = self.shapes[i]

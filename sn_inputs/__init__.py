@@ -137,6 +137,14 @@ LATTICE_ABSORBERS = ((1, 1), (3, 1), (5, 1), (2, 2), (4, 2), (1, 3), (5, 3),
 LATTICE_SOURCE = (3, 3)
 MAT_WHITE, MAT_BLUE, MAT_RED = 0, 1, 2
 LATTICE_REGIONS = ("white", "blue", "red")
+# squares S_l = [-l, l]^2 of QoI-1/2 (Sec. 3.1), l = 1.5 and 2.5, in [0,7]^2:
+# (x_lo, x_hi, y_lo, y_hi); their edges are grid lines when n is a multiple of 7
+LATTICE_QOI_SQUARES = ((2.0, 5.0, 2.0, 5.0), (1.0, 6.0, 1.0, 6.0))
+
+
+def lattice_extra(n: int) -> dict:
+    """The QoI squares, on grids where they follow cell faces (n multiple of 7)."""
+    return {"boxes": LATTICE_QOI_SQUARES} if n % 7 == 0 else {}
 
 
 def lattice_block_material(bi: np.ndarray, bj: np.ndarray) -> np.ndarray:
@@ -159,14 +167,16 @@ def lattice_materials_table(sigma_a_blue=10.0, sigma_s_white=1.0, sigma_s_red=1.
 
 def lattice_problem(n: int, sigma_a_blue=10.0, sigma_s_scatter=1.0, t_end=3.2) -> Problem:
     """Lattice checkerboard on an n x n Cartesian grid over [0,7]^2, vacuum
-    boundaries, psi0 = 0, T = 3.2. Cells are classified by their centre."""
+    boundaries, psi0 = 0, T = 3.2. Cells are classified by their centre. When n
+    is a multiple of 7 the QoI squares S_1.5, S_2.5 are attached as boxes."""
     mesh = CartesianMesh(nx=n, ny=n, x0=0.0, y0=0.0, dx=7.0 / n, dy=7.0 / n)
     xc, yc = mesh.centres()
     mat = lattice_block_material(np.floor(xc).astype(int), np.floor(yc).astype(int))
     sa, ss, q = lattice_materials_table(sigma_a_blue, sigma_s_scatter, sigma_s_scatter)
     m = Materials(sigma_a=sa, sigma_s=ss, Q=q, cell_mat=mat,
                   cell_region=mat.copy(), region_names=LATTICE_REGIONS)
-    return Problem(mesh=mesh, materials=m, boundary=Boundary(), t_end=t_end, name=f"lattice{n}")
+    return Problem(mesh=mesh, materials=m, boundary=Boundary(), t_end=t_end, name=f"lattice{n}",
+                   extra=lattice_extra(n))
 
 
 def lattice_dp2_nominal():
@@ -198,7 +208,8 @@ def lattice_dp2_problem(n: int, sigma_a_blocks, sigma_s_blocks, q_red=1.0, t_end
     Q[7 * LATTICE_SOURCE[1] + LATTICE_SOURCE[0]] = q_red
     m = Materials(sigma_a=sa.T.ravel().copy(), sigma_s=ss.T.ravel().copy(), Q=Q, cell_mat=mat,
                   cell_region=region, region_names=LATTICE_REGIONS)
-    return Problem(mesh=mesh, materials=m, boundary=Boundary(), t_end=t_end, name=f"lattice{n}_dp2")
+    return Problem(mesh=mesh, materials=m, boundary=Boundary(), t_end=t_end, name=f"lattice{n}_dp2",
+                   extra=lattice_extra(n))
 
 
 def lattice_triangle_problem(n: int, jitter=0.0, seed=0, t_end=3.2) -> Problem:

@@ -135,3 +135,33 @@ def test_null_handles_are_rejected(rt):
     assert lib.rt_batch_run(None, 1) == rt.RT_EINVAL
     lib.rt_destroy(None)
     lib.rt_batch_destroy(None)
+
+
+@pytest.mark.parametrize("boxes,msg", [
+    (((2.0, 5.0, 2.0, 5.05),), "grid line"),         # edge between grid lines
+    (((0.0, 5.0, 2.0, 5.0),), "grid line"),          # on the domain boundary
+    (((2.0, 7.0, 2.0, 5.0),), "grid line"),
+    (((5.0, 2.0, 2.0, 5.0),), "x_lo < x_hi"),
+    (((2.0, 5.0, 2.0, 5.0),) * 5, "n_boxes"),
+    (((2.0, 5.0, float("nan"), 5.0),), "finite"),
+])
+def test_create_rejects_bad_qoi_boxes(rt, boxes, msg):
+    p = si.lattice_problem(14)
+    p.extra = {"boxes": boxes}
+    with pytest.raises(rt.RTError) as e:
+        _create(rt, p, rt.rt_quad_product(2, 4))
+    assert e.value.code == rt.RT_EINVAL and msg in rt.rt_last_error()
+
+
+def test_qoi_boxes_need_a_cartesian_mesh(rt):
+    t = si.enclosure_problem(6)
+    t.extra = {"boxes": ((0.2, 0.6, 0.2, 0.6),)}
+    with pytest.raises(rt.RTError) as e:
+        _create(rt, t, rt.rt_quad_product(2, 4))
+    assert e.value.code == rt.RT_EINVAL and "Cartesian" in rt.rt_last_error()
+
+
+def test_qoi_struct_layout(rt):
+    # the header's rt_qoi_t: 392 bytes, box entries last
+    assert C.sizeof(rt.rt_qoi_t) == 392
+    assert rt.rt_qoi_t.box_out_int.offset == 392 - 8 * rt.RT_MAX_BOXES

@@ -50,6 +50,13 @@ def check_qoi(q, acc, S, n_regions, scale):
     assert rel(q["mass"], S["mass"]) <= QOI_TOL
     assert abs(q["outflow_int"] - acc.outflow_int) <= QOI_TOL * max(abs(acc.outflow_int), 1e-3 * scale)
     assert abs(q["outflow_now"] - S["outflow"]) <= QOI_TOL * max(abs(S["outflow"]), 1e-3 * scale)
+    # QoI boxes (Sec. 3.1 QoI-1/2), when the problem has them
+    nb = len(S.get("box_out", ()))
+    assert len(q["box_out_now"]) == nb
+    for b in range(nb):
+        assert abs(q["box_out_now"][b] - S["box_out"][b]) <= QOI_TOL * max(abs(S["box_out"][b]), 1e-3 * scale), b
+        assert abs(q["box_out_int"][b] - acc.box_out_int[b]) <= \
+            QOI_TOL * max(abs(acc.box_out_int[b]), 1e-3 * scale), b
 
 
 def run_pair(rt, problem, n_p, n_phi, order, integrator, steps, psi0=None, storage=0, dt=0.0, tile_y=0, tile_x=0):
@@ -206,6 +213,75 @@ def test_muscl_heun_lattice_mass_balance_and_symmetry(rt):
     assert abs(bal / q["source_int"] - 1) < 1e-5
     ph = phi.reshape(56, 56)
     assert np.max(np.abs(ph - ph[:, ::-1])) <= 1e-5 * ph.max()
+
+
+# ------------------------------------------------------------------ QoI boxes (Sec. 3.1 QoI-1/2)
+BOXES = ((2.0, 5.0, 2.0, 5.0), (1.0, 6.0, 1.0, 6.0),      # the squares S_1.5, S_2.5
+         (0.125, 0.25, 3.0, 6.875),                      # one cell wide, next to the x- boundary
+         (4.5, 6.875, 0.125, 1.0))                       # next to two boundaries
+
+
+@pytest.mark.parametrize("order,integrator,n_p,n_phi", [(1, "euler", 4, 16), (2, "heun", 4, 32), (2, "euler", 2, 16),
+                                                        (1, "heun", 8, 16)])
+def test_box_outflow_matches_the_oracle(rt, order, integrator, n_p, n_phi):
+    """Outflow through four boxes (the paper's two squares, a one-cell-wide
+    strip and a box one cell from two domain sides) from a random state: the
+    per-box values at the final state and their time integrals, against the
+    oracle; 56^2 cells (dx = 1/8), ragged tiles."""
+    p = si.lattice_problem(56)
+    p.extra = {"boxes": BOXES}
+    integ = rt.RT_EULER if integrator == "euler" else rt.RT_HEUN
+    psi0 = si.random_psi(p.mesh.n_cells, n_p * n_phi, seed=21)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, n_p, n_phi, order, integ, 9, psi0=psi0,
+                                                  dt=0.5 * p.mesh.dx, tile_y=24)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    assert len(q["box_out_now"]) == 4 and np.all(q["box_out_now"] > 0) and np.all(q["box_out_int"] > 0)
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+@pytest.mark.parametrize("quad", ["tess8", "prod12x40"])
+def test_box_outflow_of_the_lattice_squares(rt, quad):
+    """The lattice from psi = 0 with the squares S_1.5 and S_2.5 (QoI-1/2),
+    MUSCL Heun; the tessellation rule of order 8, and a product rule whose
+    ordinates are stored regrouped by quadrant (the box kernel reads the
+    internal order)."""
+    p = si.lattice_problem(42, t_end=2.0)
+    if quad == "tess8":
+        quad_lib, quad_or = rt.rt_quad_tessellation(8), oracle.tessellation_quadrature(8)
+    else:
+        quad_lib, quad_or = rt.rt_quad_product(12, 40), oracle.product_quadrature(12, 40)
+    s = rt.Solver(p, quad_lib, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    s.step()
+    q, info = s.qoi(), s.info
+    s.close()
+    assert info.regrouped == (quad != "tess8")
+    op = oracle.CartesianOracle(p, quad_or, order=2)
+    n = int(info.n_steps)
+    _, acc, S = oracle.run(op, np.zeros((p.mesh.n_cells, len(quad_or[0]))), info.dt, n, "heun")
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+    assert q["box_out_int"][0] > q["box_out_int"][1] > 0
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_box_outflow_batched_equals_alone_bitwise(rt, storage):
+    """Problems with and without boxes and with different N_t in one batch (so
+    the box launches of finished problems are masked): every box value equals
+    the problem solved alone, bit for bit."""
+    probs = [si.lattice_problem(28, t_end=0.6), si.lattice_problem(30, t_end=1.0), si.lattice_problem(35, t_end=1.4)]
+    probs[1].extra = {}
+    quads = [rt.rt_quad_product(2, 16), rt.rt_quad_product(4, 16), rt.rt_quad_product(2, 32)]
+    dts = [0.5 * pr.mesh.dx for pr in probs]
+    b = rt.Batch(probs, quads, order=2, integrator=rt.RT_HEUN, dts=dts, storage=storage)
+    b.run()
+    for i, (pr, qd) in enumerate(zip(probs, quads)):
+        s = rt.Solver(pr, qd, order=2, integrator=rt.RT_HEUN, dt=dts[i], storage=storage)
+        s.step()
+        a, c = b.qoi(i), s.qoi()
+        s.close()
+        assert len(a["box_out_now"]) == (0 if i == 1 else 2)
+        for k in ("box_out_now", "box_out_int", "mass", "outflow_int"):
+            assert np.array_equal(np.asarray(a[k]), np.asarray(c[k])), (i, k)
+    b.close()
 
 
 # ------------------------------------------------------------------ DP-2: per-block cross-sections

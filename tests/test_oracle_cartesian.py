@@ -274,3 +274,65 @@ def test_lattice_qoi_against_paper_table():
     assert abs(S["abs"][blue] / g["qoi3_absorption_at_T"]["mean"] - 1) < 0.02
     assert abs(acc.abs_int[blue] / g["qoi4_absorption_time_integrated"]["mean"] - 1) < 0.02
     assert abs(S["mass"] / g["qoi5_mass_at_T"]["mean"] - 1) < 0.02
+
+
+# ---------------------------------------------------------------- QoI boxes (Sec. 3.1 QoI-1/2)
+def _box_cells(p, box):
+    xc, yc = p.mesh.centres()
+    return (xc > box[0]) & (xc < box[1]) & (yc > box[2]) & (yc < box[3])
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_box_flow_closes_the_box_balance(order):
+    """Finite-volume conservation on the union of the cells inside a box: over
+    one Euler step, the change of the box's particle content equals dt times
+    (emission - absorption - outflow + inflow) through its boundary, with the
+    flows of box_flow. Any wrong face, side, sign, normal, length or trace in
+    box_flow breaks the identity."""
+    p = si.lattice_problem(28)
+    p.extra = {"boxes": ((2.0, 5.0, 2.0, 5.0), (1.0, 6.0, 1.0, 6.0), (0.25, 3.0, 4.5, 6.75))}
+    q = product_quadrature(4, 8)
+    op = CartesianOracle(p, q, order=order)
+    psi0 = si.random_psi(p.mesh.n_cells, 32, seed=3)
+    dt = 0.4 * p.mesh.dx
+    psi1 = psi0 + dt * op.F(psi0)
+    out, inn = op.box_flow(psi0)
+    assert np.all(out > 0) and np.all(inn > 0)
+    A = p.mesh.dx * p.mesh.dy
+    phi0, phi1 = psi0 @ q[3], psi1 @ q[3]
+    for b, box in enumerate(p.extra["boxes"]):
+        m = _box_cells(p, box)
+        change = A * (phi1[m].sum() - phi0[m].sum())
+        emitted = A * 2 * math.pi * op.Q[m].sum()
+        absorbed = A * (op.sigma_a[m] * phi0[m]).sum()
+        rhs = dt * (emitted - absorbed - out[b] + inn[b])
+        assert abs(change - rhs) <= 1e-12 * (abs(change) + dt * (out[b] + inn[b])), b
+
+
+def test_box_flow_of_the_whole_domain_is_the_boundary_outflow():
+    """With vacuum sides nothing enters the domain, so the flow out of a box
+    equal to the whole domain is the domain's boundary outflow."""
+    p = si.lattice_problem(21)
+    p.extra = {"boxes": ((0.0, 7.0, 0.0, 7.0),)}
+    op = CartesianOracle(p, product_quadrature(2, 8), order=2)
+    psi = si.random_psi(p.mesh.n_cells, 16, seed=4)
+    out, inn = op.box_flow(psi)
+    assert abs(out[0] - op.outflow(psi)) <= 1e-13 * out[0]
+    assert inn[0] == 0.0
+
+
+def test_box_flow_uniform_state_closed_form():
+    """A uniform state psi = c in every cell and ordinate (first order): the
+    flow out of a W x H box is c (H sum_k w_k |xi_k| + W sum_k w_k |eta_k|),
+    and sum_k w_k |xi_k| tends to the hemisphere integral of |xi|, pi."""
+    p = uniform_problem(20, 20, 2.0, 0.0, 0.0)
+    p.extra = {"boxes": ((0.4, 1.5, 0.2, 1.0),)}
+    q = product_quadrature(16, 64)
+    op = CartesianOracle(p, q, order=1)
+    c = 0.75
+    out, inn = op.box_flow(np.full((400, q[0].size), c))
+    W, H = 1.1, 0.8
+    assert abs(out[0] - inn[0]) <= 1e-13 * out[0]
+    assert abs(out[0] / (c * math.pi * (W + H)) - 1) < 2e-3
+    assert si.lattice_problem(70).extra["boxes"] == si.LATTICE_QOI_SQUARES
+    assert si.lattice_problem(64).extra == {}

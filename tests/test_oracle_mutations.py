@@ -69,3 +69,39 @@ def test_wrong_heun_average_is_caught():
     g_heun = 1 - sa * dt + 0.5 * (sa * dt) ** 2
     assert np.allclose(op.phi(0.5 * (psi + psi2)), 2 * math.pi * g_heun, rtol=1e-14)
     assert not np.allclose(op.phi(psi2), 2 * math.pi * g_heun, rtol=1e-6)
+
+
+def test_box_flow_from_the_outside_cell_is_caught():
+    """Taking the trace of a leaving ordinate from the cell outside the box
+    (instead of the upwind inside cell) breaks the box balance."""
+    p = si.lattice_problem(14)
+    p.extra = {"boxes": ((2.0, 5.0, 1.0, 6.0),)}
+    q = product_quadrature(2, 8)
+    psi0 = si.random_psi(p.mesh.n_cells, 16, seed=9)
+    dt = 0.4 * p.mesh.dx
+    A = p.mesh.dx * p.mesh.dy
+    xc, yc = p.mesh.centres()
+    m = (xc > 2) & (xc < 5) & (yc > 1) & (yc < 6)
+
+    class OutsideTrace(CartesianOracle):
+        def traces(self, psi):
+            Tx, Ty = super().traces(psi)
+            P = psi.reshape(self.ny, self.nx, self.M)
+            Tx = Tx.copy()
+            Tx[:, 10, :] = np.where(self.xi > 0, P[:, 10, :], Tx[:, 10, :])   # x+ side (face 10 at x = 5)
+            return Tx, Ty
+
+        def F(self, psi):
+            return CartesianOracle.F(self, psi)
+
+    def residual(op):
+        good = CartesianOracle(p, q, order=1)
+        psi1 = psi0 + dt * good.F(psi0)
+        out, inn = op.box_flow(psi0)
+        phi0, phi1 = psi0 @ q[3], psi1 @ q[3]
+        change = A * (phi1[m].sum() - phi0[m].sum())
+        rhs = dt * (A * 2 * math.pi * good.Q[m].sum() - A * (good.sigma_a[m] * phi0[m]).sum() - out[0] + inn[0])
+        return abs(change - rhs) / abs(change)
+
+    assert residual(CartesianOracle(p, q, order=1)) < 1e-12
+    assert residual(OutsideTrace(p, q, order=1)) > 1e-3
