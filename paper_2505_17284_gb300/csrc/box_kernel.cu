@@ -20,8 +20,20 @@ namespace {
 
 constexpr int kBoxThreads = 256;
 
+// Four consecutive stored values (16-byte aligned for FP32, 8-byte for BF16) as floats.
+template <typename T> __device__ __forceinline__ void load4(const T* p, float (&v)[4]);
+template <> __device__ __forceinline__ void load4<float>(const float* p, float (&v)[4]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+template <> __device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 x = *reinterpret_cast<const uint2*>(p);
+  v[0] = __uint_as_float(x.x << 16); v[1] = __uint_as_float(x.x & 0xffff0000u);
+  v[2] = __uint_as_float(x.y << 16); v[3] = __uint_as_float(x.y & 0xffff0000u);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kBoxThreads)
+__global__ void __launch_bounds__(kBoxThreads, 4)
     box_outflow_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items, int stage) {
   const WorkItem it = items[blockIdx.x];
   const InstDesc& d = descs[it.inst];
@@ -46,6 +58,9 @@ __global__ void __launch_bounds__(kBoxThreads)
   double acc[kMaxBox];
 #pragma unroll
   for (int b = 0; b < kMaxBox; ++b) acc[b] = 0.0;
+  // one face per warp at a time; each lane takes 4 consecutive ordinates per
+  // pass (one 16-byte load for FP32, 8 bytes for BF16), and loads a cell only
+  // for ordinates that leave the box
   for (int f = it.a + warp; f < it.a + it.b; f += kBoxThreads / 32) {
     const int4 fc = d.box_faces[f];
     const int box = fc.w & 0xff, side = fc.w >> 8;
@@ -56,16 +71,33 @@ __global__ void __launch_bounds__(kBoxThreads)
     const float sgn = (side & 1) ? 1.f : -1.f;
     float s = 0.f;
 #pragma unroll 4
-    for (int k = lane; k < Mpad; k += 32) {
-      // loads unconditional so that the unrolled iterations overlap
-      const float on = sgn * dir[k];         // omega_k . n_f
-      const float c = Store<T>::load(pin + k);
-      const float a = Store<T>::load(pout + k) - c, bb = c - Store<T>::load(pfar + k);
-      // slope toward the face: minmod(outside - inside, inside - far)
-      const float mm = (a * bb > 0.f) ? (fabsf(a) < fabsf(bb) ? a : bb) : 0.f;
-      const float tr = second ? fmaf(0.5f, mm, c) : c;
-      s = fmaf(on > 0.f ? d.w[k] * on : 0.f, tr, s);
+    for (int k0 = 4 * lane; k0 < Mpad; k0 += 128) {
+      const float4 dv = *reinterpret_cast<const float4*>(dir + k0);
+      const float4 wv = *reinterpret_cast<const float4*>(d.w + k0);
+      const float on[4] = {sgn * dv.x, sgn * dv.y, sgn * dv.z, sgn * dv.w};   // omega_k . n_f
+      const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
+      if (on[0] > 0.f || on[1] > 0.f || on[2] > 0.f || on[3] > 0.f) {
+        float c[4], o[4], g[4];
+        load4<T>(pin + k0, c);
+        if (second) {
+          load4<T>(pout + k0, o);
+          load4<T>(pfar + k0, g);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float tr = c[v];
+          if (second) {
+            // slope toward the face: minmod(outside - inside, inside - far)
+            const float a = o[v] - c[v], bb = c[v] - g[v];
+            const float mm = (a * bb > 0.f) ? (fabsf(a) < fabsf(bb) ? a : bb) : 0.f;
+            tr = fmaf(0.5f, mm, c[v]);
+          }
+          s = fmaf(on[v] > 0.f ? wk[v] * on[v] : 0.f, tr, s);
+        }
+      }
     }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
     const double face = (double)s * (double)((side < 2) ? ly : lx);
 #pragma unroll
     for (int b = 0; b < kMaxBox; ++b)
@@ -76,10 +108,10 @@ __global__ void __launch_bounds__(kBoxThreads)
   __shared__ double red[kBoxThreads / 32][kMaxBox];
   __shared__ double tot[kMaxBox];
   __shared__ uint32_t s_last;
+  // (every lane of a warp holds the warp's sums after the shuffles)
+  if (lane == 0) {
 #pragma unroll
-  for (int b = 0; b < kMaxBox; ++b) {
-    const double v = warp_sum_d(acc[b]);
-    if (lane == 0) red[warp][b] = v;
+    for (int b = 0; b < kMaxBox; ++b) red[warp][b] = acc[b];
   }
   __syncthreads();
   if (threadIdx.x < kMaxBox) {

@@ -14,7 +14,7 @@
 
 namespace rtk {
 
-constexpr int kBoxFacesPerItem = 32;    // QoI-box faces per work item (4 per warp)
+constexpr int kBoxFacesPerItem = 8;     // QoI-box faces per work item (one per warp)
 
 void set_error(const char* fmt, ...);
 void clear_error();
