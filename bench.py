@@ -256,8 +256,8 @@ def run_ours(args, spec):
     updates = dof * K * world
     value = updates / (ms * 1e-3)
     bpu = bytes_per_update(order, integ, storage)
-    # one launch per stage (QoI-box work items ride in the same launch)
-    launches_per_step = info.stages_per_step
+    # each stage launch is followed by the QoI-box launch when the problem has boxes
+    launches_per_step = info.stages_per_step * (2 if info.n_box_items else 1)
     achieved_gbs = dof * bpu * K / (ms * 1e-3) / 1e9
     peaks = {}
     try:

@@ -211,8 +211,8 @@ typedef struct {
                         caller's order does not give sign-uniform chunks and the padding adds at most
                         1/8; M_pad is then the padded count). rt_get_psi / rt_set_psi always use the
                         caller's order; rt_device_state exposes the internal one. */
-  int32_t n_box_items; /* QoI boxes: work items (8 faces each) that each stage launch carries after
-                          its tiles (included in n_work_items); 0 without boxes */
+  int32_t n_box_items; /* QoI boxes: work items of the box-outflow launch that follows each stage
+                          (0: no boxes, no such launch) */
 } rt_info_t;
 
 typedef struct rt_solver rt_solver;
@@ -251,8 +251,7 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
  * enqueueing. Each step is one launch (Euler) or two (Heun stages). */
 rt_status rt_step(rt_solver* s, int64_t n);
 
-/* Synchronise the stream and copy the QoIs to *out (392 bytes); with QoI boxes
- * one small launch first evaluates box_out_now of the current state. Returns
+/* Synchronise the stream and copy the QoIs to *out (392 bytes). Returns
  * RT_ETIMEOUT / RT_ENONFINITE (and enters the error state) if a kernel
  * reported one. */
 rt_status rt_qoi(rt_solver* s, rt_qoi_t* out);

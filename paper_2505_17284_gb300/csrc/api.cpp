@@ -21,7 +21,7 @@ struct rt_solver {
   InstDesc* d_desc = nullptr;
   WorkItem* d_stage_items = nullptr;
   WorkItem* d_init_items = nullptr;
-  WorkItem* d_box_items = nullptr;     // QoI-box read-back evaluation items (none: nullptr)
+  WorkItem* d_box_items = nullptr;     // QoI boxes (none: nullptr)
   int64_t host_step = 0;               // steps enqueued
   bool failed = false;
   cudaGraphExec_t graph = nullptr;
@@ -41,7 +41,8 @@ rt_status launch_steps_direct(rt_solver* s, int64_t n, cudaStream_t stream) {
   const Instance& I = s->I;
   for (int64_t i = 0; i < n; ++i) {
     rt_status st = launch_step(s->d_desc, s->d_stage_items, (int)I.stage_items.size(), I.kind, I.integrator,
-                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream, I.uni);
+                               I.storage, I.order, I.run, I.cvec, I.ly, I.vec, stream, I.uni, s->d_box_items,
+                               (int)I.box_items.size());
     if (st != RT_OK) return st;
   }
   return RT_OK;
@@ -77,12 +78,8 @@ rt_status read_state(rt_solver* s, InstState* h) { return read_inst_state(s->I, 
 
 rt_status run_init(rt_solver* s) {
   const Instance& I = s->I;
-  cudaError_t e = launch_init(s->d_desc, s->d_init_items, (int)I.init_items.size(), I.vec, I.storage, s->stream);
-  if (e != cudaSuccess) {
-    set_error("init launch failed: %s", cudaGetErrorString(e));
-    return RT_ECUDA;
-  }
-  return RT_OK;
+  return launch_init_all(s->d_desc, s->d_init_items, (int)I.init_items.size(), s->d_box_items,
+                         (int)I.box_items.size(), I.vec, I.storage, s->stream);
 }
 
 size_t elem_size(const Instance& I) { return I.storage == RT_BF16 ? 2 : 4; }
@@ -178,10 +175,8 @@ rt_status rt_qoi(rt_solver* s, rt_qoi_t* out) {
   clear_error();
   if (!s || !out) { set_error("solver and out are required"); return RT_EINVAL; }
   if (s->failed) { set_error("solver is in its error state"); return RT_ESTATE; }
-  rt_status st = eval_boxes(s->d_desc, s->d_box_items, (int)s->I.box_items.size(), s->I.storage, s->stream);
-  if (st != RT_OK) return fail(s, st);
   InstState h;
-  st = read_state(s, &h);
+  rt_status st = read_state(s, &h);
   if (st != RT_OK) return fail(s, st);
   fill_qoi(s->I, h, out);
   return RT_OK;

@@ -26,6 +26,7 @@ namespace {
 struct Group {
   int kind, order, integrator, run, cvec, vec, uni, ly_max;
   int offset, count;
+  int box_offset, box_count;   // QoI-box work items of the group's problems
 };
 
 struct Slot {
@@ -33,7 +34,7 @@ struct Slot {
   std::unique_ptr<DeviceArena> arena;
   Instance inst;
   WorkItem* d_init_items = nullptr;
-  WorkItem* d_box_items = nullptr;   // QoI-box read-back evaluation (descriptor pointer offset by slot)
+  WorkItem* d_box_items = nullptr;   // for the initial state (descriptor pointer offset by slot)
   int64_t done = 0;   // steps enqueued
 };
 
@@ -52,6 +53,8 @@ struct rt_batch {
   InstDesc* d_desc = nullptr;         // [capacity]
   WorkItem* d_items = nullptr;
   size_t items_cap = 0;
+  WorkItem* d_box_list = nullptr;     // QoI-box work items of the current membership
+  size_t box_cap = 0;
   // work list and graph of the current membership
   bool dirty = true;
   std::vector<Group> groups;
@@ -126,11 +129,9 @@ rt_status add_in_slot(rt_batch* b, const rt_problem& P, int i) {
     return undo(RT_ECUDA);
   }
   if ((st = prepare_instance_kernels(I, I.ly)) != RT_OK) return undo(st);
-  cudaError_t e = launch_init(b->d_desc + i, S.d_init_items, (int)I.init_items.size(), I.vec, I.storage, b->stream);
-  if (e != cudaSuccess) {
-    set_error("init launch failed: %s", cudaGetErrorString(e));
-    return undo(RT_ECUDA);
-  }
+  if ((st = launch_init_all(b->d_desc + i, S.d_init_items, (int)I.init_items.size(), S.d_box_items, (int)hb.size(),
+                            I.vec, I.storage, b->stream)) != RT_OK)
+    return undo(st);
   InstState h;
   if ((st = read_inst_state(I, b->stream, &h)) != RT_OK) return undo(st);
   S.used = true;
@@ -151,12 +152,13 @@ rt_status rebuild(rt_batch* b) {
     by_variant[std::make_tuple(I.kind, I.order, I.integrator, I.run, I.cvec, I.vec, I.uni)].push_back(i);
     b->members.push_back(i);
   }
-  std::vector<WorkItem> items;
+  std::vector<WorkItem> items, box_items;
   b->groups.clear();
   for (auto& kv : by_variant) {
     Group g{};
     std::tie(g.kind, g.order, g.integrator, g.run, g.cvec, g.vec, g.uni) = kv.first;
     g.offset = (int)items.size();
+    g.box_offset = (int)box_items.size();
     g.ly_max = 1;
     for (int i : kv.second) {
       const Instance& I = b->slots[i].inst;
@@ -165,8 +167,13 @@ rt_status rebuild(rt_batch* b) {
         w.inst = i;
         items.push_back(w);
       }
+      for (WorkItem w : I.box_items) {
+        w.inst = i;
+        box_items.push_back(w);
+      }
     }
     g.count = (int)items.size() - g.offset;
+    g.box_count = (int)box_items.size() - g.box_offset;
     rt_status pst = prepare_instance_kernels(b->slots[kv.second[0]].inst, g.ly_max);
     if (pst != RT_OK) return pst;
     b->groups.push_back(g);
@@ -182,6 +189,24 @@ rt_status rebuild(rt_batch* b) {
     if (st != RT_OK) return st;
     b->d_items = (WorkItem*)p;
     b->items_cap = cap;
+  }
+  if (box_items.size() > b->box_cap) {
+    cudaStreamSynchronize(b->stream);
+    if (b->d_box_list) b->shared.release(b->d_box_list);
+    b->d_box_list = nullptr;
+    b->box_cap = 0;
+    void* p = nullptr;
+    const size_t cap = std::max<size_t>(box_items.size() * 2, 256);
+    rt_status st = b->shared.get(cap * sizeof(WorkItem), &p);
+    if (st != RT_OK) return st;
+    b->d_box_list = (WorkItem*)p;
+    b->box_cap = cap;
+  }
+  if (!box_items.empty() &&
+      cudaMemcpyAsync(b->d_box_list, box_items.data(), box_items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess) {
+    set_error("copying the box work list failed");
+    return RT_ECUDA;
   }
   if (!items.empty()) {
     cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
@@ -200,7 +225,8 @@ rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream) {
   for (int64_t i = 0; i < n; ++i) {
     for (const Group& g : b->groups) {
       rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, g.integrator, b->storage, g.order,
-                                 g.run, g.cvec, g.ly_max, g.vec, stream, g.uni);
+                                 g.run, g.cvec, g.ly_max, g.vec, stream, g.uni,
+                                 g.box_count ? b->d_box_list + g.box_offset : nullptr, g.box_count);
       if (st != RT_OK) return st;
     }
   }
@@ -396,13 +422,10 @@ rt_status rt_batch_qoi(rt_batch* b, int32_t i, rt_qoi_t* out) {
   if (!b || !out) { set_error("batch and out are required"); return RT_EINVAL; }
   if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
   if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
-  const Slot& S = b->slots[i];
-  rt_status st = eval_boxes(b->d_desc + i, S.d_box_items, (int)S.inst.box_items.size(), b->storage, b->stream);
-  if (st != RT_OK) return batch_fail(b, st);
   InstState h;
-  st = read_inst_state(S.inst, b->stream, &h);
+  rt_status st = read_inst_state(b->slots[i].inst, b->stream, &h);
   if (st != RT_OK) return batch_fail(b, st);
-  fill_qoi(S.inst, h, out);
+  fill_qoi(b->slots[i].inst, h, out);
   return RT_OK;
 }
 

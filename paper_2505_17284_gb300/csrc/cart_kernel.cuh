@@ -35,7 +35,6 @@
 
 #include <type_traits>
 
-#include "box_device.cuh"
 #include "device_common.cuh"
 
 namespace rtk {
@@ -884,24 +883,6 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   cart_epilogue<TX, STAGE>(d, it, phi_out, tile_acc, red, x0, ya, nrows, bacc);
 }
 
-// QoI-box work item of a stage launch: the outflow through the box boundaries
-// (Sec. 3.1 QoI-1/2) of the stage's INPUT state, which no CTA of this launch
-// writes, handed to the shared finalize with the stage's weight. These items
-// come after the tiles of their instance, so they run in the launch's tail.
-template <int STAGE, typename T>
-__device__ __noinline__ void cart_box_item(const InstDesc& d, const WorkItem& it, uint8_t* smem) {
-  const int in_buf = (STAGE == STAGE_EULER) ? d.st->parity : (STAGE == STAGE_HEUN1 ? 0 : 1);
-  double* red = reinterpret_cast<double*>(smem);   // [kCartWarps * kMaxBox], then finalize scratch
-  double part[kMaxBox];
-  box_face_sums<kCartThreads, T>(d, it, reinterpret_cast<const T*>(d.psi[in_buf]), red, part);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int b = 0; b < kMaxBox; ++b) red[b] = part[b];
-  }
-  __syncthreads();
-  finalize_item<kCartThreads>(d, it, red, STAGE, red + NQ, kItemBox);
-}
-
 template <int ORDER, int R, int V, int STAGE, typename T, bool UNI>
 __global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
     cart_stage_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
@@ -914,10 +895,6 @@ __global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
   extern __shared__ __align__(128) uint8_t smem_raw[];
   // TMA destinations want 128-byte alignment; the launch adds 128 bytes of slack
   uint8_t* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  if (it.type == kItemBox) {
-    cart_box_item<STAGE, T>(d, it, smem);
-    return;
-  }
   const int x0 = it.a * L::TX;
   const int ya = it.b * d.ly;
   const bool xb = (x0 - L::H < 0) || (x0 + L::TX + L::H > d.nx);

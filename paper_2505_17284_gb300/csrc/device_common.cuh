@@ -230,31 +230,15 @@ __device__ __forceinline__ void block_reduce_q(const double (&acc)[NQ], int nq, 
   __syncthreads();
 }
 
-// Write this work item's QoI partial, and if it is the last item of its
-// instance in this launch, reduce all partials in item order and apply the
-// time-integration update of `stage`. Partial rows use the compact order
-// (abs per region, mass, outflow, box outflow per box); kind kItemTile gives
-// red[0..n_regions+2) for the item's output state, kind kItemBox gives
-// red[0..n_boxes) for the launch's input state. The output-state integrands
-// enter through S_cur / S_mid as before; the box outflow of the input state is
-// added to the time integral with the stage's own weight (Euler dt, each Heun
-// stage dt/2), which is the same sum. Must be called by all threads.
+// Write this work item's QoI partial (red[0..nq)), and if it is the last item of
+// its instance in this launch, reduce all partials in item order and apply the
+// time-integration update of `stage`. Must be called by all threads.
 template <int NT>
 __device__ void finalize_item(const InstDesc& d, const WorkItem& it, const double* red, int stage,
-                              double* scratch /*[NT/32][NQ]*/, int kind = kItemTile) {
+                              double* scratch /*[NT/32][NQ]*/) {
   __shared__ uint32_t s_last;
-  const int nq0 = d.n_regions + 2;
-  const int nq = nq0 + d.n_boxes;
-  if (threadIdx.x < NQ) {
-    const int q = threadIdx.x;
-    double v = 0.0;
-    if (kind == kItemTile) {
-      if (q < nq0) v = red[q];
-    } else if (q >= nq0 && q < nq) {
-      v = red[q - nq0];
-    }
-    d.partials[(size_t)it.item * NQ + q] = v;
-  }
+  const int nq = d.n_regions + 2;
+  if (threadIdx.x < NQ) d.partials[(size_t)it.item * NQ + threadIdx.x] = (threadIdx.x < nq) ? red[threadIdx.x] : 0.0;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -277,37 +261,31 @@ __device__ void finalize_item(const InstDesc& d, const WorkItem& it, const doubl
   block_reduce_q<NT>(acc, nq, scratch);
   if (threadIdx.x == 0) {
     InstState* st = d.st;
-    double S[kQBox], B[kMaxBox];
-    // map compact order (regions..., mass, outflow, boxes...) to the NQ layout
+    double S[NQ];
+    // map compact order (regions..., mass, outflow) to the NQ layout
 #pragma unroll
-    for (int q = 0; q < kQBox; ++q) S[q] = 0.0;
+    for (int q = 0; q < NQ; ++q) S[q] = 0.0;
     for (int r = 0; r < d.n_regions; ++r) S[r] = scratch[r];
     S[kQMass] = scratch[d.n_regions];
     S[kQOut] = scratch[d.n_regions + 1];
-#pragma unroll
-    for (int b = 0; b < kMaxBox; ++b) B[b] = (b < d.n_boxes) ? scratch[nq0 + b] : 0.0;
     const double dt = d.dt_d;
     if (stage == STAGE_EULER) {
-      for (int q = 0; q < kQBox; ++q) st->I[q] += dt * st->S_cur[q];
-      for (int q = 0; q < kQBox; ++q) st->S_cur[q] = S[q];
-      for (int b = 0; b < kMaxBox; ++b) st->I[kQBox + b] += dt * B[b];
+      for (int q = 0; q < NQ; ++q) st->I[q] += dt * st->S_cur[q];
+      for (int q = 0; q < NQ; ++q) st->S_cur[q] = S[q];
       st->step += 1;
       st->parity ^= 1;
     } else if (stage == STAGE_HEUN1) {
-      for (int q = 0; q < kQBox; ++q) st->I[q] += 0.5 * dt * st->S_cur[q];
-      for (int q = 0; q < kQBox; ++q) st->S_mid[q] = S[q];
-      for (int b = 0; b < kMaxBox; ++b) st->I[kQBox + b] += 0.5 * dt * B[b];
+      for (int q = 0; q < NQ; ++q) st->I[q] += 0.5 * dt * st->S_cur[q];
+      for (int q = 0; q < NQ; ++q) st->S_mid[q] = S[q];
     } else if (stage == STAGE_HEUN2) {
-      for (int q = 0; q < kQBox; ++q) st->I[q] += 0.5 * dt * st->S_mid[q];
-      for (int q = 0; q < kQBox; ++q) st->S_cur[q] = S[q];
-      for (int b = 0; b < kMaxBox; ++b) st->I[kQBox + b] += 0.5 * dt * B[b];
+      for (int q = 0; q < NQ; ++q) st->I[q] += 0.5 * dt * st->S_mid[q];
+      for (int q = 0; q < NQ; ++q) st->S_cur[q] = S[q];
       st->step += 1;
     } else {  // STAGE_INIT
-      for (int q = 0; q < kQBox; ++q) st->S_cur[q] = S[q];
+      for (int q = 0; q < NQ; ++q) st->S_cur[q] = S[q];
     }
     bool finite = isfinite(S[kQMass]) && isfinite(S[kQOut]);
     for (int r = 0; r < d.n_regions; ++r) finite = finite && isfinite(S[r]);
-    for (int b = 0; b < d.n_boxes; ++b) finite = finite && isfinite(B[b]);
     if (!finite && st->status == DEV_OK) st->status = DEV_NONFINITE;
     st->ticket = 0u;
     __threadfence();

@@ -603,23 +603,22 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     if ((s = arena.get((size_t)n_cells * 4, &p)) != RT_OK) return s;
     I.phi[b] = (float*)p;
   }
-  // QoI boxes: device face list; work items of kBoxFacesPerItem faces, both
-  // appended to the stage launch (after the tiles; every item of the instance
-  // then counts toward the one finalize) and as the read-back evaluation list
+  if ((s = arena.get(sizeof(InstState), &p)) != RT_OK) return s;
+  I.st = (InstState*)p;
+  const size_t n_part = std::max(I.stage_items.size(), I.init_items.size());
+  if ((s = arena.get(n_part * NQ * sizeof(double), &p)) != RT_OK) return s;
+  I.partials = (double*)p;
+  // QoI boxes: work items of kBoxFacesPerItem faces
   I.n_boxes = mat->n_boxes;
   I.box_items.clear();
   int4* d_faces = nullptr;
+  double* d_box_part = nullptr;
   if (!box_faces.empty()) {
     const int nf = (int)box_faces.size();
     const int n_it = (nf + kBoxFacesPerItem - 1) / kBoxFacesPerItem;
-    const int n_tiles = (int)I.stage_items.size();
-    for (WorkItem& w : I.stage_items) w.count = n_tiles + n_it;
     for (int g = 0; g < n_it; ++g) {
       WorkItem w{};
       w.inst = 0; w.a = g * kBoxFacesPerItem; w.b = std::min(kBoxFacesPerItem, nf - w.a);
-      w.type = kItemBox;
-      w.item = n_tiles + g; w.count = n_tiles + n_it;
-      I.stage_items.push_back(w);
       w.item = g; w.count = n_it;
       I.box_items.push_back(w);
     }
@@ -629,12 +628,11 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     d_faces = (int4*)p;
     RT_CUDA_TRY(cudaMemcpyAsync(d_faces, keep.back().data(), box_faces.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                 stream));
+    if ((s = arena.get((size_t)n_it * kMaxBox * sizeof(double), &p)) != RT_OK) return s;
+    d_box_part = (double*)p;
+    RT_CUDA_TRY(cudaMemsetAsync(d_box_part, 0, (size_t)n_it * kMaxBox * sizeof(double), stream));
   }
-  if ((s = arena.get(sizeof(InstState), &p)) != RT_OK) return s;
-  I.st = (InstState*)p;
-  const size_t n_part = std::max(I.stage_items.size(), I.init_items.size());
-  if ((s = arena.get(n_part * NQ * sizeof(double), &p)) != RT_OK) return s;
-  I.partials = (double*)p;
+
   // host images of per-cell and per-ordinate data (kept alive until the stream syncs)
   keep.emplace_back(3 * (size_t)I.Mpad * sizeof(float));
   float* hq = reinterpret_cast<float*>(keep.back().data());
@@ -740,6 +738,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     D.sig_a_f[m] = (float)sa;
   }
   D.box_faces = d_faces;
+  D.box_partials = d_box_part;
   D.n_boxes = I.n_boxes;
   D.n_box_faces = (int32_t)box_faces.size();
   I.device_bytes = arena.bytes;
@@ -748,7 +747,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
 
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
                       int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream,
-                      int uni) {
+                      int uni, const WorkItem* d_box_items, int n_box_items) {
   const int stages[2] = {integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
   const int n_st = integrator == RT_HEUN ? 2 : 1;
   for (int i = 0; i < n_st; ++i) {
@@ -761,16 +760,24 @@ rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_ite
       set_error("stage launch failed: %s", cudaGetErrorString(e));
       return RT_ECUDA;
     }
+    if (n_box_items > 0) {
+      e = launch_box_outflow(d_desc, d_box_items, n_box_items, stages[i], storage, stream);
+      if (e != cudaSuccess) {
+        set_error("box outflow launch failed: %s", cudaGetErrorString(e));
+        return RT_ECUDA;
+      }
+    }
   }
   return RT_OK;
 }
 
-rt_status eval_boxes(const InstDesc* d_desc, const WorkItem* d_box_items, int n_box_items, int storage,
-                     cudaStream_t stream) {
-  if (n_box_items <= 0) return RT_OK;
-  cudaError_t e = launch_box_eval(d_desc, d_box_items, n_box_items, storage, stream);
+rt_status launch_init_all(const InstDesc* d_desc, const WorkItem* d_init_items, int n_init_items,
+                          const WorkItem* d_box_items, int n_box_items, int vec, int storage, cudaStream_t stream) {
+  cudaError_t e = launch_init(d_desc, d_init_items, n_init_items, vec, storage, stream);
+  if (e == cudaSuccess && n_box_items > 0)
+    e = launch_box_outflow(d_desc, d_box_items, n_box_items, STAGE_INIT, storage, stream);
   if (e != cudaSuccess) {
-    set_error("box outflow evaluation failed: %s", cudaGetErrorString(e));
+    set_error("init launch failed: %s", cudaGetErrorString(e));
     return RT_ECUDA;
   }
   return RT_OK;
@@ -821,8 +828,8 @@ void fill_qoi(const Instance& I, const InstState& h, rt_qoi_t* out) {
   out->source_int = out->t * I.source_rate;
   out->n_boxes = I.n_boxes;
   for (int b = 0; b < I.n_boxes; ++b) {
-    out->box_out_now[b] = h.S_cur[kQBox + b];
-    out->box_out_int[b] = h.I[kQBox + b];
+    out->box_out_now[b] = h.B_cur[b];
+    out->box_out_int[b] = h.B_I[b];
   }
 }
 

@@ -63,9 +63,7 @@ struct Instance {
   std::vector<WorkItem> stage_items;   // inst field set by the owner
   std::vector<WorkItem> init_items;
   int32_t n_boxes = 0;                 // QoI boxes
-  // read-back evaluation items of the box faces (item 0..n-1; the stage launch
-  // carries the same faces as kItemBox entries of stage_items)
-  std::vector<WorkItem> box_items;
+  std::vector<WorkItem> box_items;     // box outflow work items (inst field set by the owner)
   // device buffers
   void* psi[2] = {nullptr, nullptr};
   float* phi[2] = {nullptr, nullptr};
@@ -87,13 +85,14 @@ int device_sm_count();
 
 // Launch the stage(s) of one time step for the given instances' work items.
 // `run`/`cvec` select the Cartesian variant, `vec` the triangle vector width.
+// d_box_items/n_box_items: the QoI-box work items of the same instances (after
+// every stage, the box outflow of its output state).
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
                       int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream,
-                      int uni = 0);
-// Box outflow of the current state into the box columns of InstState::S_cur
-// (before a QoI read-back); no-op without boxes.
-rt_status eval_boxes(const InstDesc* d_desc, const WorkItem* d_box_items, int n_box_items, int storage,
-                     cudaStream_t stream);
+                      int uni = 0, const WorkItem* d_box_items = nullptr, int n_box_items = 0);
+// Initial-state launches: phi and QoI integrands, then the box outflow.
+rt_status launch_init_all(const InstDesc* d_desc, const WorkItem* d_init_items, int n_init_items,
+                          const WorkItem* d_box_items, int n_box_items, int vec, int storage, cudaStream_t stream);
 rt_status prepare_instance_kernels(const Instance& I, int ly_max);
 
 // Synchronise `stream` and read an instance's device state; maps device status

@@ -54,7 +54,7 @@ __global__ void noalloc_setup_kernel(const __grid_constant__ InstDesc desc, int 
     w.b = i / n_strips;
     w.item = i;
     w.count = n_items;
-    w.type = kItemTile;
+    w.pad = 0;
     items[i] = w;
   }
   // the tensor maps were written through the generic proxy; the stage kernel

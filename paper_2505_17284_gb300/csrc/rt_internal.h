@@ -9,6 +9,7 @@
 //   state         InstState (step, buffer parity, status, FP64 QoI sums)
 //   partials      FP64 per-work-item QoI partial sums [n_items][NQ]
 //   box_faces     QoI boxes: one record per face of a box boundary (Cartesian)
+//   box_partials  FP64 per-work-item box outflow partial sums [n_box_items][kMaxBox]
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -21,8 +22,7 @@ constexpr int kMaxReg = 16;
 constexpr int kMaxBox = 4;             // QoI boxes (outflow through their boundary)
 constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
-constexpr int kQBox = kMaxReg + 2;     // index of the first box outflow
-constexpr int NQ = kMaxReg + 2 + kMaxBox;   // QoI vector: abs[16], mass, outflow, box[4]
+constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
 constexpr int kChunk = 32;             // ordinates per chunk (one per lane)
 constexpr int kMaxUniChunks = 64;      // chunk-uniform variant: at most this many ordinate chunks
 
@@ -41,10 +41,14 @@ struct InstState {
   int64_t timeout_where; // diagnostic: encoded position of a wait that ran out
   double S_cur[NQ];      // integrands at psi^n
   double S_mid[NQ];      // Heun: integrands at psi^(1)
-  double I[NQ];          // time integrals (abs, -, outflow, box outflow)
-  // Box columns: the stage launch adds the box outflow of its INPUT state to I
-  // with the stage's weight; S_cur's box columns hold the outflow of the
-  // current state only after an explicit evaluation (read-back).
+  double I[NQ];          // time integrals (abs, -, outflow)
+  // QoI boxes: outflow through each box boundary, updated by the box kernel
+  uint32_t box_ticket;   // box work items finished in the current launch
+  int32_t pad1;
+  int64_t box_step;      // step at the box kernel's last update (tells a masked stage)
+  double B_cur[kMaxBox]; // at psi^n
+  double B_mid[kMaxBox]; // Heun: at psi^(1)
+  double B_I[kMaxBox];   // time integrals
 };
 
 struct alignas(128) InstDesc {
@@ -87,6 +91,7 @@ struct alignas(128) InstDesc {
   // neighbour along the normal, box | side << 8} (side 0..3: the box's x-, x+,
   // y-, y+ side, named by its outward normal)
   const int4* box_faces;
+  double* box_partials;         // [n_box_items][kMaxBox]
   int32_t n_boxes, n_box_faces;
 };
 
@@ -96,10 +101,8 @@ struct WorkItem {
   int32_t b;          // Cartesian stage: segment; cell-range kernels: number of cells
   int32_t item;       // index of this item within its instance (partials row)
   int32_t count;      // items of this instance in this launch (last one finalizes)
-  int32_t type;       // kItemTile, or kItemBox: QoI-box faces a .. a+b-1 (Cartesian stage launch)
+  int32_t pad;
 };
-constexpr int32_t kItemTile = 0;
-constexpr int32_t kItemBox = 1;
 
 // Launchers (defined in the .cu files). All enqueue on `stream`.
 // Cartesian stage kernel variants: run = cells per thread in x (tile width 8*run),
@@ -116,11 +119,11 @@ cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, in
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
-// Outflow through the QoI boxes of the current state into the box columns of
-// InstState::S_cur (a read-back evaluation; no time integral changes). Work
-// items: a = first face, b = number of faces, item 0..count-1.
-cudaError_t launch_box_eval(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int storage,
-                            cudaStream_t stream);
+// Outflow through the QoI boxes of the state a stage just wrote (stage =
+// STAGE_INIT: the current state), with the stage's time-integration update.
+// Work items: a = first face, b = number of faces.
+cudaError_t launch_box_outflow(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
+                               int storage, cudaStream_t stream);
 // FP64 [cell][M] (caller's ordinate order) <-> storage [cell][Mpad] (internal
 // order); inv: internal slot -> caller ordinate or -1, kmap: caller ordinate ->
 // slot (device arrays; NULL when the orders agree).
