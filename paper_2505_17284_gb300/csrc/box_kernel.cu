@@ -1,17 +1,20 @@
 // Outflow through the boundaries of axis-aligned QoI boxes (the lattice's
 // QoI-1 and QoI-2 of Sec. 3.1, through the squares S_l): for a face f of the
 // boundary of box b, with n_f the normal pointing out of the box and l_f its
-// length, the box gains l_f sum_k w_k max(omega_k . n_f, 0) psi_hat_k,f, where
+// length, the box loses l_f sum_k w_k max(omega_k . n_f, 0) psi_hat_k,f, where
 // psi_hat is the scheme's upwind trace (Sec. 4.2): for an ordinate leaving the
 // box the upwind cell is the inside one, so the trace is its value at first
 // order and its MUSCL-minmod reconstruction toward the face at second order.
 //
-// The kernel runs after every stage on the state that stage wrote (and once on
-// the initial state), reads three cells per face (inside, outside, and the
-// inside cell's other neighbour along the normal), and closes with the same
-// time-integration update as the other QoIs: Euler adds dt S(psi^n), Heun
-// dt/2 (S(psi^n) + S(psi^(1))). Partial sums are FP64 per work item, reduced
-// by the last item of the instance in item order (deterministic).
+// One launch per time step, after the step's last stage (and one on the
+// initial state). It reads three cells per face (inside, outside, and the
+// inside cell's other neighbour along the normal) and applies the time
+// integration with the scheme's weights: Euler adds dt S(psi^n); Heun adds
+// dt/2 (S(psi^n) + S(psi^(1))), and since stage 2 leaves psi^(1) in buffer 1
+// next to psi^(n+1) in buffer 0, the Heun launch evaluates both states.
+// S(psi^n) is carried from the previous launch. Partial sums are FP64 per
+// work item, reduced by the last item of the instance in item order
+// (deterministic).
 #include "device_common.cuh"
 
 namespace rtk {
@@ -19,6 +22,8 @@ namespace rtk {
 namespace {
 
 constexpr int kBoxThreads = 256;
+constexpr int kBoxFacesPerWarp = kBoxFacesPerItem / (kBoxThreads / 32);
+static_assert(kBoxFacesPerWarp == 2, "two faces per warp");
 
 // Four consecutive stored values (16-byte aligned for FP32, 8-byte for BF16) as floats.
 template <typename T> __device__ __forceinline__ void load4(const T* p, float (&v)[4]);
@@ -32,92 +37,124 @@ template <> __device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bflo
   v[2] = __uint_as_float(x.y << 16); v[3] = __uint_as_float(x.y & 0xffff0000u);
 }
 
+// stage: STAGE_EULER or STAGE_INIT (the current state, buffer `parity`) or
+// STAGE_HEUN2 (after a Heun step: psi^(1) in buffer 1, psi^(n+1) in buffer 0).
 template <typename T>
-__global__ void __launch_bounds__(kBoxThreads, 4)
+__global__ void __launch_bounds__(kBoxThreads, 3)
     box_outflow_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items, int stage) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WorkItem it = items[blockIdx.x];
   const InstDesc& d = descs[it.inst];
   InstState* st = d.st;
-  // skip when the stage before was masked (a finished or failed instance of a
-  // batch): Heun stage 1 ran iff the stage kernel's own test passes (it does
-  // not change the step); Euler and Heun stage 2 ran iff the step advanced
-  if (stage == STAGE_HEUN1) {
-    if (st->step >= d.n_steps || st->status != DEV_OK) return;
-  } else if (stage != STAGE_INIT) {
-    if (st->step == st->box_step) return;
+  // Prologue, independent of the stage before: the warp's two faces. With a
+  // programmatic launch it overlaps the end of that stage; griddepcontrol.wait
+  // then waits for the stage grid to complete and its writes to be visible
+  // (without a programmatic dependency it returns at once).
+  int4 fc[kBoxFacesPerWarp];
+#pragma unroll
+  for (int j = 0; j < kBoxFacesPerWarp; ++j) {
+    const int f = it.a + warp + j * (kBoxThreads / 32);
+    fc[j] = (f < it.a + it.b) ? d.box_faces[f] : make_int4(0, 0, 0, -1);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // the stage's output: Heun stage 1 writes buffer 1; every other stage leaves the
-  // current state in the buffer named by the parity (Heun keeps it at 0)
-  const int buf = (stage == STAGE_HEUN1) ? 1 : st->parity;
-  const T* __restrict__ psi = reinterpret_cast<const T*>(d.psi[buf]);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // skip when the step before was masked (a finished or failed instance of a
+  // batch): it ran iff the step counter advanced since the last update
+  if (stage != STAGE_INIT && st->step == st->box_step) return;
+  const bool heun = stage == STAGE_HEUN2;
+  const T* psiA = reinterpret_cast<const T*>(d.psi[heun ? 1 : st->parity]);   // evaluation 0
+  const T* psiB = reinterpret_cast<const T*>(d.psi[0]);                        // evaluation 1 (Heun)
   const int Mpad = d.Mpad;
   const bool second = d.order == 2;
   const float lx = (float)d.dx_d, ly = (float)d.dy_d;
 
-  double acc[kMaxBox];
+  // Jobs of two (face, state) pairs whose loads overlap: the two faces of the
+  // warp for one state, or (Heun) one face for both states, face after face.
+  // Each lane takes 4 consecutive ordinates per pass (one 16-byte load for
+  // FP32, 8 bytes for BF16) and loads a cell only for ordinates that leave.
+  double acc[2][kMaxBox];
 #pragma unroll
-  for (int b = 0; b < kMaxBox; ++b) acc[b] = 0.0;
-  // one face per warp at a time; each lane takes 4 consecutive ordinates per
-  // pass (one 16-byte load for FP32, 8 bytes for BF16), and loads a cell only
-  // for ordinates that leave the box
-  for (int f = it.a + warp; f < it.a + it.b; f += kBoxThreads / 32) {
-    const int4 fc = d.box_faces[f];
-    const int box = fc.w & 0xff, side = fc.w >> 8;
-    const T* pin = psi + (size_t)fc.x * Mpad;
-    const T* pout = psi + (size_t)fc.y * Mpad;
-    const T* pfar = psi + (size_t)fc.z * Mpad;
-    const float* dir = (side < 2) ? d.xi : d.eta;
-    const float sgn = (side & 1) ? 1.f : -1.f;
-    float s = 0.f;
-#pragma unroll 4
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int b = 0; b < kMaxBox; ++b) acc[e][b] = 0.0;
+  const int rounds = heun ? kBoxFacesPerWarp : 1;
+  for (int r = 0; r < rounds; ++r) {
+    int4 jf[2];
+    const T* jp[2];
+    float sgn[2], s[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      jf[j] = heun ? fc[r] : fc[j];
+      jp[j] = (heun && j == 1) ? psiB : psiA;
+      // omega . n = sgn * xi (x- / x+ sides) or sgn * eta (y- / y+); 0: no face
+      sgn[j] = (jf[j].w < 0) ? 0.f : (((jf[j].w >> 8) & 1) ? 1.f : -1.f);
+      s[j] = 0.f;
+    }
     for (int k0 = 4 * lane; k0 < Mpad; k0 += 128) {
-      const float4 dv = *reinterpret_cast<const float4*>(dir + k0);
+      const float4 xv = *reinterpret_cast<const float4*>(d.xi + k0);
+      const float4 ev = *reinterpret_cast<const float4*>(d.eta + k0);
       const float4 wv = *reinterpret_cast<const float4*>(d.w + k0);
-      const float on[4] = {sgn * dv.x, sgn * dv.y, sgn * dv.z, sgn * dv.w};   // omega_k . n_f
+      const float xs[4] = {xv.x, xv.y, xv.z, xv.w}, es[4] = {ev.x, ev.y, ev.z, ev.w};
       const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
-      if (on[0] > 0.f || on[1] > 0.f || on[2] > 0.f || on[3] > 0.f) {
-        float c[4], o[4], g[4];
-        load4<T>(pin + k0, c);
-        if (second) {
-          load4<T>(pout + k0, o);
-          load4<T>(pfar + k0, g);
-        }
+      float on[2][4], c[2][4], o[2][4], g[2][4];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const bool xside = ((jf[j].w >> 8) & 2) == 0;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          float tr = c[v];
+          on[j][v] = sgn[j] * (xside ? xs[v] : es[v]);
+          c[j][v] = o[j][v] = g[j][v] = 0.f;
+        }
+        if (on[j][0] > 0.f || on[j][1] > 0.f || on[j][2] > 0.f || on[j][3] > 0.f) {
+          load4<T>(jp[j] + (size_t)jf[j].x * Mpad + k0, c[j]);
           if (second) {
-            // slope toward the face: minmod(outside - inside, inside - far)
-            const float a = o[v] - c[v], bb = c[v] - g[v];
-            const float mm = (a * bb > 0.f) ? (fabsf(a) < fabsf(bb) ? a : bb) : 0.f;
-            tr = fmaf(0.5f, mm, c[v]);
+            load4<T>(jp[j] + (size_t)jf[j].y * Mpad + k0, o[j]);
+            load4<T>(jp[j] + (size_t)jf[j].z * Mpad + k0, g[j]);
           }
-          s = fmaf(on[v] > 0.f ? wk[v] * on[v] : 0.f, tr, s);
         }
       }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float tr = c[j][v];
+          if (second) {
+            // slope toward the face: minmod(outside - inside, inside - far)
+            const float a = o[j][v] - c[j][v], bb = c[j][v] - g[j][v];
+            const float mm = (a * bb > 0.f) ? (fabsf(a) < fabsf(bb) ? a : bb) : 0.f;
+            tr = fmaf(0.5f, mm, c[j][v]);
+          }
+          s[j] = fmaf(on[j][v] > 0.f ? wk[v] * on[j][v] : 0.f, tr, s[j]);
+        }
     }
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    const double face = (double)s * (double)((side < 2) ? ly : lx);
+    for (int j = 0; j < 2; ++j) {
+      float v = s[j];
 #pragma unroll
-    for (int b = 0; b < kMaxBox; ++b)
-      if (b == box) acc[b] += face;
+      for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+      if (jf[j].w < 0) continue;
+      const int box = jf[j].w & 0xff, side = jf[j].w >> 8;
+      const double face = (double)v * (double)((side < 2) ? ly : lx);
+      const int e = (heun && j == 1) ? 1 : 0;
+#pragma unroll
+      for (int b = 0; b < kMaxBox; ++b)
+        if (b == box) acc[e][b] += face;
+    }
   }
 
-  // block reduction in a fixed order
-  __shared__ double red[kBoxThreads / 32][kMaxBox];
-  __shared__ double tot[kMaxBox];
+  // block reduction in a fixed order (every lane of a warp holds the warp's sums)
+  constexpr int NB = 2 * kMaxBox;
+  __shared__ double red[kBoxThreads / 32][NB];
+  __shared__ double tot[NB];
   __shared__ uint32_t s_last;
-  // (every lane of a warp holds the warp's sums after the shuffles)
   if (lane == 0) {
 #pragma unroll
-    for (int b = 0; b < kMaxBox; ++b) red[warp][b] = acc[b];
+    for (int q = 0; q < NB; ++q) red[warp][q] = acc[q / kMaxBox][q % kMaxBox];
   }
   __syncthreads();
-  if (threadIdx.x < kMaxBox) {
+  if (threadIdx.x < NB) {
     double v = 0.0;
     for (int w = 0; w < kBoxThreads / 32; ++w) v += red[w][threadIdx.x];
-    d.box_partials[(size_t)it.item * kMaxBox + threadIdx.x] = v;
+    d.box_partials[(size_t)it.item * NB + threadIdx.x] = v;
   }
   __threadfence();
   __syncthreads();
@@ -130,19 +167,20 @@ __global__ void __launch_bounds__(kBoxThreads, 4)
   __threadfence();
   // all threads: item i goes to thread i mod kBoxThreads, then the fixed-order
   // block reduction
+  double part[NB];
 #pragma unroll
-  for (int b = 0; b < kMaxBox; ++b) acc[b] = 0.0;
+  for (int q = 0; q < NB; ++q) part[q] = 0.0;
   for (int i = threadIdx.x; i < it.count; i += kBoxThreads) {
 #pragma unroll
-    for (int b = 0; b < kMaxBox; ++b) acc[b] += __ldcg(d.box_partials + (size_t)i * kMaxBox + b);
+    for (int q = 0; q < NB; ++q) part[q] += __ldcg(d.box_partials + (size_t)i * NB + q);
   }
 #pragma unroll
-  for (int b = 0; b < kMaxBox; ++b) {
-    const double v = warp_sum_d(acc[b]);
-    if (lane == 0) red[warp][b] = v;
+  for (int q = 0; q < NB; ++q) {
+    const double v = warp_sum_d(part[q]);
+    if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
-  if (threadIdx.x < kMaxBox) {
+  if (threadIdx.x < NB) {
     double v = 0.0;
     for (int w = 0; w < kBoxThreads / 32; ++w) v += red[w][threadIdx.x];
     tot[threadIdx.x] = v;
@@ -151,21 +189,19 @@ __global__ void __launch_bounds__(kBoxThreads, 4)
   if (threadIdx.x == 0) {
     const double dt = d.dt_d;
     for (int b = 0; b < kMaxBox; ++b) {
-      const double S = (b < d.n_boxes) ? tot[b] : 0.0;
+      const bool on = b < d.n_boxes;
+      const double S0 = on ? tot[b] : 0.0, S1 = on ? tot[kMaxBox + b] : 0.0;
       if (stage == STAGE_EULER) {
         st->B_I[b] += dt * st->B_cur[b];
-        st->B_cur[b] = S;
-      } else if (stage == STAGE_HEUN1) {
-        st->B_I[b] += 0.5 * dt * st->B_cur[b];
-        st->B_mid[b] = S;
+        st->B_cur[b] = S0;
       } else if (stage == STAGE_HEUN2) {
-        st->B_I[b] += 0.5 * dt * st->B_mid[b];
-        st->B_cur[b] = S;
+        st->B_I[b] += 0.5 * dt * (st->B_cur[b] + S0);
+        st->B_cur[b] = S1;
       } else {  // STAGE_INIT
-        st->B_cur[b] = S;
+        st->B_cur[b] = S0;
       }
     }
-    if (stage != STAGE_HEUN1) st->box_step = st->step;
+    st->box_step = st->step;
     st->box_ticket = 0u;
     __threadfence();
   }
@@ -176,11 +212,20 @@ __global__ void __launch_bounds__(kBoxThreads, 4)
 cudaError_t launch_box_outflow(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
                                int storage, cudaStream_t stream) {
   if (n_items <= 0) return cudaSuccess;
-  if (storage == 1)
-    box_outflow_kernel<__nv_bfloat16><<<n_items, kBoxThreads, 0, stream>>>(d_desc, d_items, stage);
-  else
-    box_outflow_kernel<float><<<n_items, kBoxThreads, 0, stream>>>(d_desc, d_items, stage);
-  return cudaGetLastError();
+  // programmatic dependent launch: the CTAs may start (and run the prologue)
+  // while the stage before finishes; the kernel waits for it before reading
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)n_items);
+  cfg.blockDim = dim3(kBoxThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (storage == 1) return cudaLaunchKernelEx(&cfg, box_outflow_kernel<__nv_bfloat16>, d_desc, d_items, stage);
+  return cudaLaunchKernelEx(&cfg, box_outflow_kernel<float>, d_desc, d_items, stage);
 }
 
 }  // namespace rtk

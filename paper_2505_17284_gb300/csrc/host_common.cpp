@@ -628,9 +628,9 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     d_faces = (int4*)p;
     RT_CUDA_TRY(cudaMemcpyAsync(d_faces, keep.back().data(), box_faces.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                 stream));
-    if ((s = arena.get((size_t)n_it * kMaxBox * sizeof(double), &p)) != RT_OK) return s;
+    if ((s = arena.get((size_t)n_it * 2 * kMaxBox * sizeof(double), &p)) != RT_OK) return s;
     d_box_part = (double*)p;
-    RT_CUDA_TRY(cudaMemsetAsync(d_box_part, 0, (size_t)n_it * kMaxBox * sizeof(double), stream));
+    RT_CUDA_TRY(cudaMemsetAsync(d_box_part, 0, (size_t)n_it * 2 * kMaxBox * sizeof(double), stream));
   }
 
   // host images of per-cell and per-ordinate data (kept alive until the stream syncs)
@@ -760,12 +760,13 @@ rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_ite
       set_error("stage launch failed: %s", cudaGetErrorString(e));
       return RT_ECUDA;
     }
-    if (n_box_items > 0) {
-      e = launch_box_outflow(d_desc, d_box_items, n_box_items, stages[i], storage, stream);
-      if (e != cudaSuccess) {
-        set_error("box outflow launch failed: %s", cudaGetErrorString(e));
-        return RT_ECUDA;
-      }
+  }
+  // QoI boxes: one launch after the step's last stage
+  if (n_box_items > 0) {
+    cudaError_t e = launch_box_outflow(d_desc, d_box_items, n_box_items, stages[n_st - 1], storage, stream);
+    if (e != cudaSuccess) {
+      set_error("box outflow launch failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
     }
   }
   return RT_OK;

@@ -14,7 +14,6 @@
 
 namespace rtk {
 
-constexpr int kBoxFacesPerItem = 8;     // QoI-box faces per work item (one per warp)
 
 void set_error(const char* fmt, ...);
 void clear_error();
@@ -85,8 +84,8 @@ int device_sm_count();
 
 // Launch the stage(s) of one time step for the given instances' work items.
 // `run`/`cvec` select the Cartesian variant, `vec` the triangle vector width.
-// d_box_items/n_box_items: the QoI-box work items of the same instances (after
-// every stage, the box outflow of its output state).
+// d_box_items/n_box_items: the QoI-box work items of the same instances (one
+// launch after the step's last stage).
 rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int kind, int integrator,
                       int storage, int order, int run, int cvec, int ly_max, int vec, cudaStream_t stream,
                       int uni = 0, const WorkItem* d_box_items = nullptr, int n_box_items = 0);

@@ -9,7 +9,7 @@
 //   state         InstState (step, buffer parity, status, FP64 QoI sums)
 //   partials      FP64 per-work-item QoI partial sums [n_items][NQ]
 //   box_faces     QoI boxes: one record per face of a box boundary (Cartesian)
-//   box_partials  FP64 per-work-item box outflow partial sums [n_box_items][kMaxBox]
+//   box_partials  FP64 per-work-item box outflow partial sums [n_box_items][2 * kMaxBox]
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -20,6 +20,7 @@ namespace rtk {
 constexpr int kMaxMat = 64;
 constexpr int kMaxReg = 16;
 constexpr int kMaxBox = 4;             // QoI boxes (outflow through their boundary)
+constexpr int kBoxFacesPerItem = 16;   // QoI-box faces per work item of the box kernel
 constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
 constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
@@ -47,7 +48,6 @@ struct InstState {
   int32_t pad1;
   int64_t box_step;      // step at the box kernel's last update (tells a masked stage)
   double B_cur[kMaxBox]; // at psi^n
-  double B_mid[kMaxBox]; // Heun: at psi^(1)
   double B_I[kMaxBox];   // time integrals
 };
 
@@ -91,7 +91,7 @@ struct alignas(128) InstDesc {
   // neighbour along the normal, box | side << 8} (side 0..3: the box's x-, x+,
   // y-, y+ side, named by its outward normal)
   const int4* box_faces;
-  double* box_partials;         // [n_box_items][kMaxBox]
+  double* box_partials;         // [n_box_items][2 * kMaxBox]
   int32_t n_boxes, n_box_faces;
 };
 
@@ -119,9 +119,10 @@ cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, in
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
-// Outflow through the QoI boxes of the state a stage just wrote (stage =
-// STAGE_INIT: the current state), with the stage's time-integration update.
-// Work items: a = first face, b = number of faces.
+// Outflow through the QoI boxes after a time step (stage = STAGE_EULER, or
+// STAGE_HEUN2 after a whole Heun step) with the step's time-integration
+// update, or of the current state (STAGE_INIT). Work items: a = first face,
+// b = number of faces (at most kBoxFacesPerItem).
 cudaError_t launch_box_outflow(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
                                int storage, cudaStream_t stream);
 // FP64 [cell][M] (caller's ordinate order) <-> storage [cell][Mpad] (internal
