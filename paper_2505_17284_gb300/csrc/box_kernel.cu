@@ -8,7 +8,8 @@
 //
 // One launch per time step, after the step's last stage (and one on the
 // initial state). It reads three cells per face (inside, outside, and the
-// inside cell's other neighbour along the normal) and applies the time
+// inside cell's other neighbour along the normal), only in the blocks of
+// ordinates that hold leaving ones, and applies the time
 // integration with the scheme's weights: Euler adds dt S(psi^n); Heun adds
 // dt/2 (S(psi^n) + S(psi^(1))), and since stage 2 leaves psi^(1) in buffer 1
 // next to psi^(n+1) in buffer 0, the Heun launch evaluates both states.
@@ -22,8 +23,9 @@ namespace rtk {
 namespace {
 
 constexpr int kBoxThreads = 256;
-constexpr int kBoxFacesPerWarp = kBoxFacesPerItem / (kBoxThreads / 32);
-static_assert(kBoxFacesPerWarp == 2, "two faces per warp");
+constexpr int kBoxTasksPerWarp = kBoxTasksPerItem / (kBoxThreads / 32);
+static_assert(kBoxTasksPerWarp * (kBoxThreads / 32) == kBoxTasksPerItem && kBoxTasksPerWarp % 2 == 0,
+              "whole pairs of tasks per warp");
 
 // Four consecutive stored values (16-byte aligned for FP32, 8-byte for BF16) as floats.
 template <typename T> __device__ __forceinline__ void load4(const T* p, float (&v)[4]);
@@ -39,116 +41,126 @@ template <> __device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bflo
 
 // stage: STAGE_EULER or STAGE_INIT (the current state, buffer `parity`) or
 // STAGE_HEUN2 (after a Heun step: psi^(1) in buffer 1, psi^(n+1) in buffer 0).
+// A task is one face and one block of 128 ordinates holding at least one
+// ordinate that leaves through it: record {inside cell, outside cell, the
+// inside cell's other neighbour along the normal, box | side << 8 | block << 12}.
+// Lane l takes ordinates 128 block + 4 l .. +3; a warp runs its tasks two at a
+// time with every load of the pair in flight, and keeps FP32 sums per state
+// and box in each lane until the end.
 template <typename T>
-__global__ void __launch_bounds__(kBoxThreads, 3)
+__global__ void __launch_bounds__(kBoxThreads, 2)
     box_outflow_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items, int stage) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WorkItem it = items[blockIdx.x];
   const InstDesc& d = descs[it.inst];
   InstState* st = d.st;
-  // Prologue, independent of the stage before: the warp's two faces. With a
-  // programmatic launch it overlaps the end of that stage; griddepcontrol.wait
-  // then waits for the stage grid to complete and its writes to be visible
-  // (without a programmatic dependency it returns at once).
-  int4 fc[kBoxFacesPerWarp];
-#pragma unroll
-  for (int j = 0; j < kBoxFacesPerWarp; ++j) {
-    const int f = it.a + warp + j * (kBoxThreads / 32);
-    fc[j] = (f < it.a + it.b) ? d.box_faces[f] : make_int4(0, 0, 0, -1);
+  // Prologue, independent of the stage before: the warp's task records (lane j
+  // holds task j). With a programmatic launch it overlaps the end of that
+  // stage; griddepcontrol.wait then waits for the stage grid to complete and
+  // its writes to be visible (without a programmatic dependency it returns at once).
+  int4 rec = make_int4(0, 0, 0, -1);
+  if (lane < kBoxTasksPerWarp) {
+    const int t = it.a + warp + lane * (kBoxThreads / 32);
+    if (t < it.a + it.b) rec = d.box_tasks[t];
   }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // skip when the step before was masked (a finished or failed instance of a
   // batch): it ran iff the step counter advanced since the last update
   if (stage != STAGE_INIT && st->step == st->box_step) return;
   const bool heun = stage == STAGE_HEUN2;
-  const T* psiA = reinterpret_cast<const T*>(d.psi[heun ? 1 : st->parity]);   // evaluation 0
-  const T* psiB = reinterpret_cast<const T*>(d.psi[0]);                        // evaluation 1 (Heun)
+  const T* psiA = reinterpret_cast<const T*>(d.psi[heun ? 1 : st->parity]);   // state 0
+  const T* psiB = reinterpret_cast<const T*>(d.psi[0]);                        // state 1 (Heun)
   const int Mpad = d.Mpad;
   const bool second = d.order == 2;
   const float lx = (float)d.dx_d, ly = (float)d.dy_d;
 
-  // Jobs of two (face, state) pairs whose loads overlap: the two faces of the
-  // warp for one state, or (Heun) one face for both states, face after face.
-  // Each lane takes 4 consecutive ordinates per pass (one 16-byte load for
-  // FP32, 8 bytes for BF16) and loads a cell only for ordinates that leave.
-  double acc[2][kMaxBox];
+  float acc[2][kMaxBox];
 #pragma unroll
   for (int e = 0; e < 2; ++e)
 #pragma unroll
-    for (int b = 0; b < kMaxBox; ++b) acc[e][b] = 0.0;
-  const int rounds = heun ? kBoxFacesPerWarp : 1;
-  for (int r = 0; r < rounds; ++r) {
-    int4 jf[2];
-    const T* jp[2];
-    float sgn[2], s[2];
+    for (int b = 0; b < kMaxBox; ++b) acc[e][b] = 0.f;
+#pragma unroll
+  for (int r = 0; r < kBoxTasksPerWarp; r += 2) {
+    int4 tk[2];
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      jf[j] = heun ? fc[r] : fc[j];
-      jp[j] = (heun && j == 1) ? psiB : psiA;
-      // omega . n = sgn * xi (x- / x+ sides) or sgn * eta (y- / y+); 0: no face
-      sgn[j] = (jf[j].w < 0) ? 0.f : (((jf[j].w >> 8) & 1) ? 1.f : -1.f);
-      s[j] = 0.f;
+      tk[j].x = __shfl_sync(0xffffffffu, rec.x, r + j);
+      tk[j].y = __shfl_sync(0xffffffffu, rec.y, r + j);
+      tk[j].z = __shfl_sync(0xffffffffu, rec.z, r + j);
+      tk[j].w = __shfl_sync(0xffffffffu, rec.w, r + j);
     }
-    for (int k0 = 4 * lane; k0 < Mpad; k0 += 128) {
-      const float4 xv = *reinterpret_cast<const float4*>(d.xi + k0);
-      const float4 ev = *reinterpret_cast<const float4*>(d.eta + k0);
-      const float4 wv = *reinterpret_cast<const float4*>(d.w + k0);
-      const float xs[4] = {xv.x, xv.y, xv.z, xv.w}, es[4] = {ev.x, ev.y, ev.z, ev.w};
-      const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
-      float on[2][4], c[2][4], o[2][4], g[2][4];
+    float on[2][4], wl[2][4], c[2][2][4], o[2][2][4], g[2][2][4];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const bool xside = ((jf[j].w >> 8) & 2) == 0;
+    for (int j = 0; j < 2; ++j) {
+      const int side = (tk[j].w >> 8) & 3;
+      const int k = ((tk[j].w >> 12) << 7) + 4 * lane;
+      // a task slot past the item's end, or (M_pad not a multiple of 128) a lane
+      // past the last ordinate, reads nothing
+      const bool live = tk[j].w >= 0 && k < Mpad;
+      const float* dir = (side < 2) ? d.xi : d.eta;
+      const float sg = (side & 1) ? 1.f : -1.f;
+      const float l = (side < 2) ? ly : lx;
+      float4 dv = make_float4(0.f, 0.f, 0.f, 0.f), wv = dv;
+      if (live) {
+        dv = *reinterpret_cast<const float4*>(dir + k);
+        wv = *reinterpret_cast<const float4*>(d.w + k);
+      }
+      const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, ww[4] = {wv.x, wv.y, wv.z, wv.w};
+      bool any = false;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          on[j][v] = sgn[j] * (xside ? xs[v] : es[v]);
-          c[j][v] = o[j][v] = g[j][v] = 0.f;
-        }
-        if (on[j][0] > 0.f || on[j][1] > 0.f || on[j][2] > 0.f || on[j][3] > 0.f) {
-          load4<T>(jp[j] + (size_t)jf[j].x * Mpad + k0, c[j]);
-          if (second) {
-            load4<T>(jp[j] + (size_t)jf[j].y * Mpad + k0, o[j]);
-            load4<T>(jp[j] + (size_t)jf[j].z * Mpad + k0, g[j]);
-          }
-        }
+      for (int v = 0; v < 4; ++v) {
+        on[j][v] = sg * dd[v];                       // omega_k . n_f
+        wl[j][v] = on[j][v] > 0.f ? l * ww[v] * on[j][v] : 0.f;
+        any = any || on[j][v] > 0.f;
       }
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int e = 0; e < 2; ++e)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          float tr = c[j][v];
-          if (second) {
-            // slope toward the face: minmod(outside - inside, inside - far)
-            const float a = o[j][v] - c[j][v], bb = c[j][v] - g[j][v];
-            const float mm = (a * bb > 0.f) ? (fabsf(a) < fabsf(bb) ? a : bb) : 0.f;
-            tr = fmaf(0.5f, mm, c[j][v]);
-          }
-          s[j] = fmaf(on[j][v] > 0.f ? wk[v] * on[j][v] : 0.f, tr, s[j]);
+        for (int v = 0; v < 4; ++v) c[j][e][v] = o[j][e][v] = g[j][e][v] = 0.f;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (!any || (e == 1 && !heun)) continue;
+        const T* ps = e ? psiB : psiA;
+        load4<T>(ps + (size_t)tk[j].x * Mpad + k, c[j][e]);
+        if (second) {
+          load4<T>(ps + (size_t)tk[j].y * Mpad + k, o[j][e]);
+          load4<T>(ps + (size_t)tk[j].z * Mpad + k, g[j][e]);
         }
+      }
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      float v = s[j];
+      const int box = tk[j].w & 0xff;
 #pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-      if (jf[j].w < 0) continue;
-      const int box = jf[j].w & 0xff, side = jf[j].w >> 8;
-      const double face = (double)v * (double)((side < 2) ? ly : lx);
-      const int e = (heun && j == 1) ? 1 : 0;
+      for (int e = 0; e < 2; ++e) {
+        float sum = 0.f;
 #pragma unroll
-      for (int b = 0; b < kMaxBox; ++b)
-        if (b == box) acc[e][b] += face;
+        for (int v = 0; v < 4; ++v) {
+          float tr = c[j][e][v];
+          if (second) {
+            // slope toward the face: minmod(outside - inside, inside - far)
+            const float a = o[j][e][v] - c[j][e][v], bb = c[j][e][v] - g[j][e][v];
+            const float mm = (a * bb > 0.f) ? (fabsf(a) < fabsf(bb) ? a : bb) : 0.f;
+            tr = fmaf(0.5f, mm, c[j][e][v]);
+          }
+          sum = fmaf(wl[j][v], tr, sum);
+        }
+#pragma unroll
+        for (int b = 0; b < kMaxBox; ++b)
+          if (b == box) acc[e][b] += sum;
+      }
     }
   }
 
-  // block reduction in a fixed order (every lane of a warp holds the warp's sums)
+  // block reduction in a fixed order: lanes (FP64 from here), then warps
   constexpr int NB = 2 * kMaxBox;
   __shared__ double red[kBoxThreads / 32][NB];
   __shared__ double tot[NB];
   __shared__ uint32_t s_last;
-  if (lane == 0) {
 #pragma unroll
-    for (int q = 0; q < NB; ++q) red[warp][q] = acc[q / kMaxBox][q % kMaxBox];
+  for (int q = 0; q < NB; ++q) {
+    const double v = warp_sum_d((double)acc[q / kMaxBox][q % kMaxBox]);
+    if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
   if (threadIdx.x < NB) {

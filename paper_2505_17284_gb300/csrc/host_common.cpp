@@ -608,25 +608,42 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   const size_t n_part = std::max(I.stage_items.size(), I.init_items.size());
   if ((s = arena.get(n_part * NQ * sizeof(double), &p)) != RT_OK) return s;
   I.partials = (double*)p;
-  // QoI boxes: work items of kBoxFacesPerItem faces
+  // QoI boxes: tasks = (face, block of 128 ordinates holding an ordinate that
+  // leaves through the face, by the sign the kernel sees: FP32 omega . n > 0),
+  // in work items of kBoxTasksPerItem tasks
   I.n_boxes = mat->n_boxes;
   I.box_items.clear();
   int4* d_faces = nullptr;
   double* d_box_part = nullptr;
+  std::vector<int4> box_tasks;
   if (!box_faces.empty()) {
-    const int nf = (int)box_faces.size();
-    const int n_it = (nf + kBoxFacesPerItem - 1) / kBoxFacesPerItem;
+    std::vector<int> leave[4];
+    for (int sd = 0; sd < 4; ++sd)
+      for (int kb = 0; kb * 128 < I.Mpad; ++kb) {
+        bool any = false;
+        for (int k = kb * 128; k < std::min<int64_t>((int64_t)kb * 128 + 128, quad->M); ++k) {
+          const float dir = (float)(sd < 2 ? quad->xi[k] : quad->eta[k]);
+          any = any || ((sd & 1) ? dir : -dir) > 0.f;
+        }
+        if (any) leave[sd].push_back(kb);
+      }
+    for (const int4& f : box_faces)
+      for (int kb : leave[(f.w >> 8) & 3]) box_tasks.push_back(make_int4(f.x, f.y, f.z, f.w | kb << 12));
+  }
+  if (!box_tasks.empty()) {
+    const int nt = (int)box_tasks.size();
+    const int n_it = (nt + kBoxTasksPerItem - 1) / kBoxTasksPerItem;
     for (int g = 0; g < n_it; ++g) {
       WorkItem w{};
-      w.inst = 0; w.a = g * kBoxFacesPerItem; w.b = std::min(kBoxFacesPerItem, nf - w.a);
+      w.inst = 0; w.a = g * kBoxTasksPerItem; w.b = std::min(kBoxTasksPerItem, nt - w.a);
       w.item = g; w.count = n_it;
       I.box_items.push_back(w);
     }
-    keep.emplace_back(box_faces.size() * sizeof(int4));
-    std::memcpy(keep.back().data(), box_faces.data(), box_faces.size() * sizeof(int4));
-    if ((s = arena.get(box_faces.size() * sizeof(int4), &p)) != RT_OK) return s;
+    keep.emplace_back(box_tasks.size() * sizeof(int4));
+    std::memcpy(keep.back().data(), box_tasks.data(), box_tasks.size() * sizeof(int4));
+    if ((s = arena.get(box_tasks.size() * sizeof(int4), &p)) != RT_OK) return s;
     d_faces = (int4*)p;
-    RT_CUDA_TRY(cudaMemcpyAsync(d_faces, keep.back().data(), box_faces.size() * sizeof(int4), cudaMemcpyHostToDevice,
+    RT_CUDA_TRY(cudaMemcpyAsync(d_faces, keep.back().data(), box_tasks.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                 stream));
     if ((s = arena.get((size_t)n_it * 2 * kMaxBox * sizeof(double), &p)) != RT_OK) return s;
     d_box_part = (double*)p;
@@ -737,10 +754,10 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     D.sig_a[m] = sa;
     D.sig_a_f[m] = (float)sa;
   }
-  D.box_faces = d_faces;
+  D.box_tasks = d_faces;
   D.box_partials = d_box_part;
   D.n_boxes = I.n_boxes;
-  D.n_box_faces = (int32_t)box_faces.size();
+  D.n_box_tasks = (int32_t)box_tasks.size();
   I.device_bytes = arena.bytes;
   return RT_OK;
 }

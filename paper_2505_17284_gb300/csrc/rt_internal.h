@@ -8,7 +8,7 @@
 //   desc          InstDesc (tensor maps, pointers, constants)
 //   state         InstState (step, buffer parity, status, FP64 QoI sums)
 //   partials      FP64 per-work-item QoI partial sums [n_items][NQ]
-//   box_faces     QoI boxes: one record per face of a box boundary (Cartesian)
+//   box_tasks     QoI boxes: one record per (face of a box boundary, block of ordinates)
 //   box_partials  FP64 per-work-item box outflow partial sums [n_box_items][2 * kMaxBox]
 #pragma once
 #include <cuda.h>
@@ -20,7 +20,7 @@ namespace rtk {
 constexpr int kMaxMat = 64;
 constexpr int kMaxReg = 16;
 constexpr int kMaxBox = 4;             // QoI boxes (outflow through their boundary)
-constexpr int kBoxFacesPerItem = 16;   // QoI-box faces per work item of the box kernel
+constexpr int kBoxTasksPerItem = 48;   // box kernel: (face, 128-ordinate block) tasks per work item
 constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
 constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
@@ -87,12 +87,14 @@ struct alignas(128) InstDesc {
   float q_src[kMaxMat];
   float sig_a_f[kMaxMat];       // sigma_a as float (per-cell QoI terms; no FP64 in hot loops)
   double sig_a[kMaxMat];
-  // QoI boxes: face records {inside cell, outside cell, the inside cell's other
-  // neighbour along the normal, box | side << 8} (side 0..3: the box's x-, x+,
-  // y-, y+ side, named by its outward normal)
-  const int4* box_faces;
+  // QoI boxes: task records {inside cell, outside cell, the inside cell's other
+  // neighbour along the normal, box | side << 8 | block << 12}, one per face of
+  // a box boundary and block of 128 ordinates holding an ordinate that leaves
+  // through it (side 0..3: the box's x-, x+, y-, y+ side, named by its outward
+  // normal)
+  const int4* box_tasks;
   double* box_partials;         // [n_box_items][2 * kMaxBox]
-  int32_t n_boxes, n_box_faces;
+  int32_t n_boxes, n_box_tasks;
 };
 
 struct WorkItem {
@@ -122,7 +124,7 @@ cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_i
 // Outflow through the QoI boxes after a time step (stage = STAGE_EULER, or
 // STAGE_HEUN2 after a whole Heun step) with the step's time-integration
 // update, or of the current state (STAGE_INIT). Work items: a = first face,
-// b = number of faces (at most kBoxFacesPerItem).
+// b = number of tasks (at most kBoxTasksPerItem).
 cudaError_t launch_box_outflow(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
                                int storage, cudaStream_t stream);
 // FP64 [cell][M] (caller's ordinate order) <-> storage [cell][Mpad] (internal
