@@ -106,20 +106,20 @@ __global__ void __launch_bounds__(kBoxThreads, 2)
         wv = *reinterpret_cast<const float4*>(d.w + k);
       }
       const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, ww[4] = {wv.x, wv.y, wv.z, wv.w};
+      bool any = false;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         on[j][v] = sg * dd[v];                       // omega_k . n_f
         wl[j][v] = on[j][v] > 0.f ? l * ww[v] * on[j][v] : 0.f;
+        any = any || on[j][v] > 0.f;
       }
 #pragma unroll
       for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int v = 0; v < 4; ++v) c[j][e][v] = o[j][e][v] = g[j][e][v] = 0.f;
-      // the cells are loaded without waiting for the signs (the block was chosen
-      // for its leaving ordinates; entering ones get weight 0)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        if (!live || (e == 1 && !heun)) continue;
+        if (!any || (e == 1 && !heun)) continue;
         const T* ps = e ? psiB : psiA;
         load4<T>(ps + (size_t)tk[j].x * Mpad + k, c[j][e]);
         if (second) {

@@ -20,7 +20,7 @@ namespace rtk {
 constexpr int kMaxMat = 64;
 constexpr int kMaxReg = 16;
 constexpr int kMaxBox = 4;             // QoI boxes (outflow through their boundary)
-constexpr int kBoxTasksPerItem = 32;   // box kernel: (face, 128-ordinate block) tasks per work item
+constexpr int kBoxTasksPerItem = 48;   // box kernel: (face, 128-ordinate block) tasks per work item
 constexpr int kQMass = kMaxReg;        // index of the mass in a QoI vector
 constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
 constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
