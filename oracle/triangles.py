@@ -8,10 +8,20 @@ l_ij and unit normal n_ij pointing from C_i into C_j. The semi-discrete form
                        - A_i sigma_t,i psi_{k,i}
                        + A_i sigma_s,i/(2 pi) sum_l w_l psi_{l,i} + A_i Q_i
 
-with the first-order upwind trace (Eq. upwind1stOrder with R = psi):
-psi_hat = psi_i where omega . n_ij > 0, else psi_j. Boundary edges use a ghost
-cell holding psi^- (the side's inflow value for entering ordinates, 0
-otherwise), with first-order fluxes (Sec. 4.2, last paragraph).
+with the upwind trace of Eq. upwind1stOrder: psi_hat = R_i where
+omega . n_ij > 0, else R_j, both evaluated at the edge midpoint x_ij.
+First order: R = psi. Second order (the paper's production scheme, Sec. 4.2):
+R_i = psi_i + L_i g_i . r_ij with r_ij = x_ij - x_i (x_i the centroid),
+the Green-Gauss gradient g_i = (1/A_i) sum_j l_ij n_ij (psi_i + psi_j)/2 and
+the Venkatakrishnan limiter L_i = min_j L_ij of Eq. V_limiter, written as
+printed: Delta = (1/2) g_i . r_ij; for Delta > 0
+L_ij = (1/Delta) ((b^2 + e^2) Delta + 2 Delta^2 b) / (b^2 + 2 Delta^2 + b Delta + e^2)
+with b = beta_max = max_{j in S_i and i} psi_j - psi_i, for Delta < 0 the same
+with b = beta_min (the min), and L_ij = 1 for Delta = 0; e = K A_i^3, K = 1.
+Boundary edges use a ghost cell holding psi^- (the side's inflow value for
+entering ordinates, 0 otherwise): it enters the gradient and the max/min as a
+neighbour value, and fluxes through boundary edges are first order (Sec.
+4.2, last paragraph).
 
 The mesh metrics (areas, outward normals times lengths, neighbours, boundary
 sides) are derived here from the vertex list alone.
@@ -55,15 +65,39 @@ def triangle_metrics(vertices, triangles, box):
     return area, nl, nbr, side
 
 
+def venkatakrishnan(delta, beta_max, beta_min, eps):
+    """Limiter value of one edge (Eq. V_limiter as printed), elementwise."""
+    eps2 = eps * eps
+    with np.errstate(divide="ignore", invalid="ignore"):
+        up = ((beta_max ** 2 + eps2) * delta + 2 * delta ** 2 * beta_max) / \
+            (beta_max ** 2 + 2 * delta ** 2 + beta_max * delta + eps2) / delta
+        dn = ((beta_min ** 2 + eps2) * delta + 2 * delta ** 2 * beta_min) / \
+            (beta_min ** 2 + 2 * delta ** 2 + beta_min * delta + eps2) / delta
+    return np.where(delta > 0, up, np.where(delta < 0, dn, 1.0))
+
+
 class TriangleOracle:
-    def __init__(self, problem, quad, order=1):
-        if order != 1:
-            raise NotImplementedError("triangle meshes: first order only")
+    def __init__(self, problem, quad, order=1, K=1.0):
+        if order not in (1, 2):
+            raise ValueError("order must be 1 or 2")
+        self.order = order
         mesh = problem.mesh
         self.xi, self.eta, _, self.w = [np.asarray(q, dtype=np.float64) for q in quad]
         self.M = self.xi.size
         self.area, self.nl, self.nbr, self.side = triangle_metrics(mesh.vertices, mesh.triangles, mesh.box)
         self.n_cells = self.area.size
+        # second order: centroid-to-edge-midpoint vectors, the neighbour's local
+        # index of each shared edge, and the limiter's epsilon = K A^3
+        P = np.asarray(mesh.vertices, dtype=np.float64)[np.asarray(mesh.triangles)]
+        self.r = 0.5 * (P + np.roll(P, -1, axis=1)) - P.mean(axis=1)[:, None, :]     # [n, 3, 2]
+        self.nbr_edge = np.full((self.n_cells, 3), -1, dtype=np.int64)
+        for e in range(3):
+            for f in range(3):
+                j = self.nbr[:, e]
+                hit = (j >= 0)
+                hit[hit] = self.nbr[j[hit], f] == np.nonzero(hit)[0]
+                self.nbr_edge[hit, e] = f
+        self.eps = K * self.area ** 3
         m = problem.materials
         mat = np.asarray(m.cell_mat)
         self.sigma_a = np.asarray(m.sigma_a, dtype=np.float64)[mat]
@@ -86,20 +120,66 @@ class TriangleOracle:
         """Scalar flux phi_i = sum_k w_k psi_{k,i} (Eq. sn_2d)."""
         return psi @ self.w
 
-    def edge_trace(self, psi, e):
-        """Upwind trace on local edge e of every cell: [n_cells, M]."""
-        on = self.nl[:, e, 0:1] * self.xi[None, :] + self.nl[:, e, 1:2] * self.eta[None, :]
+    def neighbour_values(self, psi, e):
+        """psi of the cell across local edge e, or the ghost value psi^-: [n_cells, M]."""
         j = self.nbr[:, e]
         inside = j >= 0
         other = np.empty_like(psi)
         other[inside] = psi[j[inside]]
         other[~inside] = self.ghost[self.side[~inside, e]]
-        return np.where(on > 0.0, psi, other), on
+        return other
+
+    def gradient(self, psi):
+        """Green-Gauss gradient (gx, gy), each [n_cells, M]."""
+        gx = np.zeros_like(psi)
+        gy = np.zeros_like(psi)
+        for e in range(3):
+            avg = 0.5 * (psi + self.neighbour_values(psi, e))
+            gx += self.nl[:, e, 0:1] * avg
+            gy += self.nl[:, e, 1:2] * avg
+        return gx / self.area[:, None], gy / self.area[:, None]
+
+    def limiter(self, psi, gx, gy):
+        """Venkatakrishnan limiter L_i per cell and ordinate: [n_cells, M]."""
+        nb = [self.neighbour_values(psi, e) for e in range(3)]
+        pmax = np.maximum(psi, np.maximum(np.maximum(nb[0], nb[1]), nb[2]))
+        pmin = np.minimum(psi, np.minimum(np.minimum(nb[0], nb[1]), nb[2]))
+        L = None
+        for e in range(3):
+            delta = 0.5 * (gx * self.r[:, e, 0:1] + gy * self.r[:, e, 1:2])
+            Le = venkatakrishnan(delta, pmax - psi, pmin - psi, self.eps[:, None])
+            L = Le if L is None else np.minimum(L, Le)
+        return L
+
+    def reconstruct(self, psi):
+        """R_i at the three edge midpoints: [3][n_cells, M] (first order: psi)."""
+        if self.order == 1:
+            return [psi, psi, psi]
+        gx, gy = self.gradient(psi)
+        L = self.limiter(psi, gx, gy)
+        return [psi + L * (gx * self.r[:, e, 0:1] + gy * self.r[:, e, 1:2]) for e in range(3)]
+
+    def edge_trace(self, psi, e, R=None):
+        """Upwind trace on local edge e of every cell: [n_cells, M]. Boundary
+        edges are first order (cell value or ghost)."""
+        on = self.nl[:, e, 0:1] * self.xi[None, :] + self.nl[:, e, 1:2] * self.eta[None, :]
+        j = self.nbr[:, e]
+        inside = j >= 0
+        if R is None or self.order == 1:
+            return np.where(on > 0.0, psi, self.neighbour_values(psi, e)), on
+        mine = np.where(inside[:, None], R[e], psi)
+        other = np.empty_like(psi)
+        for f in range(3):
+            sel = inside & (self.nbr_edge[:, e] == f)
+            other[sel] = R[f][j[sel]]
+        other[~inside] = self.ghost[self.side[~inside, e]]
+        return np.where(on > 0.0, mine, other), on
 
     def flux_sum(self, psi):
+        R = self.reconstruct(psi)
         s = np.zeros_like(psi)
         for e in range(3):
-            tr, on = self.edge_trace(psi, e)
+            tr, on = self.edge_trace(psi, e, R)
             s += on * tr
         return s
 

@@ -105,3 +105,42 @@ def test_box_flow_from_the_outside_cell_is_caught():
 
     assert residual(CartesianOracle(p, q, order=1)) < 1e-12
     assert residual(OutsideTrace(p, q, order=1)) > 1e-3
+
+
+def test_limiter_without_the_half_is_caught():
+    """Delta = g.r instead of the printed (1/2) g.r changes the limiter on a
+    linear field away from the textbook values the pin derives."""
+    from oracle import TriangleOracle
+    from oracle.triangles import venkatakrishnan
+    from test_oracle_triangles import uniform_tri_problem, _phi_venkat
+
+    class NoHalf(TriangleOracle):
+        def limiter(self, psi, gx, gy):
+            nb = [self.neighbour_values(psi, e) for e in range(3)]
+            pmax = np.maximum(psi, np.maximum(np.maximum(nb[0], nb[1]), nb[2]))
+            pmin = np.minimum(psi, np.minimum(np.minimum(nb[0], nb[1]), nb[2]))
+            L = None
+            for e in range(3):
+                delta = gx * self.r[:, e, 0:1] + gy * self.r[:, e, 1:2]
+                Le = venkatakrishnan(delta, pmax - psi, pmin - psi, self.eps[:, None])
+                L = Le if L is None else np.minimum(L, Le)
+            return L
+
+    p = uniform_tri_problem(8, 1.0, 0.0, 0.0)
+    q = product_quadrature(1, 4)
+    xc, yc = p.mesh.centroids()
+    psi = (2.0 + xc + 0.3 * yc)[:, None] * np.ones((1, 4))
+
+    def worst(op):
+        gx, gy = op.gradient(psi)
+        L = op.limiter(psi, gx, gy)[:, 0]
+        err = 0.0
+        for c in np.nonzero(np.all(op.nbr >= 0, axis=1))[0]:
+            gr = op.r[c] @ np.array([1.0, 0.3])
+            bmax, bmin = max(0.0, 2 * gr.max()), min(0.0, 2 * gr.min())
+            expect = min(_phi_venkat((bmax if v > 0 else bmin) / (0.5 * v)) for v in gr if v != 0)
+            err = max(err, abs(L[c] - expect))
+        return err
+
+    assert worst(TriangleOracle(p, q, order=2)) < 1e-9
+    assert worst(NoHalf(p, q, order=2)) > 1e-2
