@@ -41,21 +41,32 @@ WORKLOADS = {
     "lattice560_muscl_heun_fp32": ("lattice", 560, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
     "lattice840_muscl_heun_fp32": ("lattice", 840, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
     "enclosure650_tri_o1_euler_fp32": ("enclosure", 650, 8, 32, 1, "euler", "fp32", 0.0, 2.6),
+    # the paper's production scheme on triangles: Green-Gauss + Venkatakrishnan, Heun
+    "enclosure1300_tri_o2_heun_fp32": ("enclosure", 1300, 8, 32, 2, "heun", "fp32", 0.0, 2.6),
+    "enclosure650_tri_o2_heun_fp32": ("enclosure", 650, 8, 32, 2, "heun", "fp32", 0.0, 2.6),
     # the paper's own angular resolution: tessellation order 22 (1936 ordinates)
     "lattice1400_muscl_heun_tess22_fp32": ("lattice", 1400, 0, 22, 2, "heun", "fp32", 0.5, 3.2),
 }
 DEFAULT = "lattice1400_muscl_heun_fp32"
 
 
-def bytes_per_update(order, integrator, storage):
+def bytes_per_update(order, integrator, storage, mesh="lattice"):
     """Algorithmic HBM bytes per cell-ordinate per step (state traffic only):
     Euler reads psi^n and writes psi^{n+1}; Heun stage 1 reads psi^n and writes
-    psi1, stage 2 reads psi1 and psi^n and writes psi^{n+1}."""
+    psi1, stage 2 reads psi1 and psi^n and writes psi^{n+1}. Second order on
+    triangles adds, per stage, the limited gradient (two FP32 values) written
+    by the gradient pass and read back by the stage pass, and the gradient
+    pass's read of the stage input."""
     es = 2 if storage == "bf16" else 4
-    return (2 if integrator == "euler" else 5) * es
+    base = (2 if integrator == "euler" else 5) * es
+    if mesh != "lattice" and order == 2:
+        stages = 1 if integrator == "euler" else 2
+        base += stages * (es + 16)
+    return base
 
 
-KERNEL_SOURCES = {"cart": ["cart_kernel.cuh", "device_common.cuh"], "tri": ["tri_kernel.cu", "device_common.cuh"]}
+KERNEL_SOURCES = {"cart": ["cart_kernel.cuh", "device_common.cuh"], "tri": ["tri_kernel.cu", "device_common.cuh"],
+                  "tri2": ["tri2_kernel.cu", "device_common.cuh"]}
 
 
 def kernel_sha(kind):
@@ -167,7 +178,7 @@ def build(n):
         op = oracle.CartesianOracle(p, Q, order=order)
     else:
         p = si.enclosure_problem(n, jitter=0.2, seed=0)
-        op = oracle.TriangleOracle(p, Q)
+        op = oracle.TriangleOracle(p, Q, order=order)
         dt = oracle.triangle_dt(op, t_end)[1]
     return p, op, dt
 n = 14 if mesh == "lattice" else 10
@@ -255,9 +266,12 @@ def run_ours(args, spec):
     dof = info.n_cells * info.M
     updates = dof * K * world
     value = updates / (ms * 1e-3)
-    bpu = bytes_per_update(order, integ, storage)
+    bpu = bytes_per_update(order, integ, storage, mesh)
     # each stage launch is followed by the QoI-box launch when the problem has boxes
-    launches_per_step = info.stages_per_step * (2 if info.n_box_items else 1)
+    # stage launches, plus one QoI-box launch per step (Cartesian problems with
+    # boxes); second order on triangles runs a gradient launch before each stage
+    launches_per_step = info.stages_per_step * (2 if (mesh != "lattice" and order == 2) else 1) + \
+        (1 if info.n_box_items else 0)
     achieved_gbs = dof * bpu * K / (ms * 1e-3) / 1e9
     peaks = {}
     try:
@@ -290,7 +304,8 @@ def run_ours(args, spec):
         h2d = n_cells * (16 + 32) + 3 * info.M_pad * 4
     d2h = QOI_BYTES
 
-    tb, traffic_src = profiled_traffic(args.workload, "cart" if mesh == "lattice" else "tri")
+    kind = "cart" if mesh == "lattice" else ("tri2" if order == 2 else "tri")
+    tb, traffic_src = profiled_traffic(args.workload, kind)
     traffic = tb * dof if tb is not None else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -309,7 +324,8 @@ def run_ours(args, spec):
                      "frac": achieved_gbs / peak, "traffic": traffic,
                      "traffic_per": "step (all stage launches), DRAM read + write bytes",
                      "traffic_source": traffic_src,
-                     "kernel": "cart_stage_kernel" if mesh == "lattice" else "tri_stage_kernel",
+                     "kernel": {"cart": "cart_stage_kernel", "tri": "tri_stage_kernel",
+                                "tri2": "tri_grad_kernel + tri_stage2_kernel"}[kind],
                      "bytes_per_update": bpu, "peak_source": f"{peak_src} hbm_gbs",
                      "achieved_basis": "algorithmic bytes per cell-ordinate x cell-ordinates x steps / event time of the steps"},
         "e2e": {"value": dof * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,

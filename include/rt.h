@@ -126,7 +126,12 @@ typedef void* (*rt_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*rt_free_fn)(void* ptr, void* ctx);
 
 /* Solver options.
- *   order: 1 (first-order upwind) or 2 (MUSCL-minmod; Cartesian only).
+ *   order: 1 (first-order upwind) or 2: on Cartesian meshes MUSCL with minmod
+ *     slopes per dimension; on triangle meshes the paper's reconstruction
+ *     (Sec. 4.2): Green-Gauss gradient, Venkatakrishnan limiter with
+ *     Delta = g.r/2 and epsilon = A^3, first-order fluxes on boundary edges
+ *     (one extra gradient launch per stage and 8 bytes per cell and ordinate
+ *     of device memory for the limited gradient).
  *   integrator: RT_EULER or RT_HEUN.  storage: RT_FP32 or RT_BF16 (psi storage;
  *     arithmetic is FP32 either way, QoI accumulation FP64).
  *   dt > 0: target step; N_t = ceil(t_end/dt - 1e-9) and dt = t_end/N_t.

@@ -163,6 +163,7 @@ static int64_t steps_for(double t_end, double dt_target) {
 struct TriMeta {
   std::vector<int4> nbr;
   std::vector<float4> geo;
+  std::vector<float4> geo2;   // second order: centroid-to-midpoint and centroid-to-neighbour vectors
   std::vector<double> area;
   double min_2a_over_p = 0;
 };
@@ -219,11 +220,16 @@ static rt_status triangle_metadata(const rt_mesh* m, const int32_t* cell_mat, co
     min_ratio = std::min(min_ratio, 2.0 * A / P);
   }
   out.min_2a_over_p = min_ratio;
+  std::vector<double> cen(2 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int c = 0; c < 2; ++c)
+      cen[2 * t + c] = (V[2 * T[3 * t] + c] + V[2 * T[3 * t + 1] + c] + V[2 * T[3 * t + 2] + c]) / 3.0;
+  out.geo2.assign(3 * nt, float4{0, 0, 0, 0});
   for (int64_t t = 0; t < nt; ++t) {
     const int32_t a[3] = {T[3 * t], T[3 * t + 1], T[3 * t + 2]};
     const double A = out.area[t];
     int32_t nb[3];
-    float ax[3], ay[3];
+    float ax[3], ay[3], rx[3], ry[3], dx[3] = {0, 0, 0}, dy[3] = {0, 0, 0};
     for (int e = 0; e < 3; ++e) {
       const int32_t p = a[e], q = a[(e + 1) % 3];
       const double px = V[2 * p], py = V[2 * p + 1], qx = V[2 * q], qy = V[2 * q + 1];
@@ -231,8 +237,12 @@ static rt_status triangle_metadata(const rt_mesh* m, const int32_t* cell_mat, co
       const double nlx = qy - py, nly = -(qx - px);
       ax[e] = (float)(nlx / A);
       ay[e] = (float)(nly / A);
+      rx[e] = (float)(0.5 * (px + qx) - cen[2 * t]);
+      ry[e] = (float)(0.5 * (py + qy) - cen[2 * t + 1]);
       if (link[3 * t + e] >= 0) {
         nb[e] = link[3 * t + e];
+        dx[e] = (float)(cen[2 * (int64_t)nb[e]] - cen[2 * t]);
+        dy[e] = (float)(cen[2 * (int64_t)nb[e] + 1] - cen[2 * t + 1]);
       } else {
         const double mx = 0.5 * (px + qx), my = 0.5 * (py + qy);
         const double dist[4] = {std::fabs(mx - xmin), std::fabs(mx - xmax), std::fabs(my - ymin), std::fabs(my - ymax)};
@@ -244,7 +254,11 @@ static rt_status triangle_metadata(const rt_mesh* m, const int32_t* cell_mat, co
     }
     out.nbr[t] = int4{nb[0], nb[1], nb[2], (int)(cell_mat[t] & 255) | ((int)(cell_reg[t] & 255) << 8)};
     out.geo[2 * t] = float4{ax[0], ay[0], ax[1], ay[1]};
-    out.geo[2 * t + 1] = float4{ax[2], ay[2], (float)A, 0.f};
+    const double eps = A * A * A;   // the limiter's epsilon = K A^3 with K = 1
+    out.geo[2 * t + 1] = float4{ax[2], ay[2], (float)A, (float)(eps * eps)};
+    out.geo2[3 * t] = float4{rx[0], ry[0], rx[1], ry[1]};
+    out.geo2[3 * t + 1] = float4{rx[2], ry[2], dx[0], dy[0]};
+    out.geo2[3 * t + 2] = float4{dx[1], dy[1], dx[2], dy[2]};
   }
   return RT_OK;
 }
@@ -458,7 +472,6 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     if (n_cells > 0x7fffffffLL) { set_error("Cartesian mesh too large"); return RT_EINVAL; }
   } else if (mesh->kind == RT_MESH_TRIANGLES) {
     n_cells = mesh->n_tri;
-    if (order != 1) { set_error("triangle meshes support order 1 only"); return RT_EINVAL; }
   } else {
     set_error("unknown mesh kind %d", mesh->kind); return RT_EINVAL;
   }
@@ -680,6 +693,8 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   uint8_t* d_reg = nullptr;
   int4* d_nbr = nullptr;
   float4* d_geo = nullptr;
+  float4* d_geo2 = nullptr;
+  float* d_lg = nullptr;
   if (I.kind == RT_MESH_CARTESIAN) {
     keep.emplace_back(2 * (size_t)n_cells);
     uint8_t* hm = reinterpret_cast<uint8_t*>(keep.back().data());
@@ -704,6 +719,18 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     d_geo = (float4*)p;
     RT_CUDA_TRY(cudaMemcpyAsync(d_nbr, hn, n_cells * sizeof(int4), cudaMemcpyHostToDevice, stream));
     RT_CUDA_TRY(cudaMemcpyAsync(d_geo, hg, 2 * n_cells * sizeof(float4), cudaMemcpyHostToDevice, stream));
+    if (order == 2) {
+      keep.emplace_back(3 * n_cells * sizeof(float4));
+      std::memcpy(keep.back().data(), tm.geo2.data(), 3 * n_cells * sizeof(float4));
+      if ((s = arena.get(3 * n_cells * sizeof(float4), &p)) != RT_OK) return s;
+      d_geo2 = (float4*)p;
+      RT_CUDA_TRY(cudaMemcpyAsync(d_geo2, keep.back().data(), 3 * n_cells * sizeof(float4), cudaMemcpyHostToDevice,
+                                  stream));
+      const size_t lg_bytes = (size_t)n_cells * 2 * I.Mpad * sizeof(float);
+      if ((s = arena.get(lg_bytes, &p)) != RT_OK) return s;
+      d_lg = (float*)p;
+      RT_CUDA_TRY(cudaMemsetAsync(d_lg, 0, lg_bytes, stream));
+    }
   }
   for (int b = 0; b < 2; ++b) {
     RT_CUDA_TRY(cudaMemsetAsync(I.psi[b], 0, psi_bytes, stream));
@@ -726,6 +753,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   D.mat = d_mat; D.region = d_reg;
   D.xi = d_quad; D.eta = d_quad + I.Mpad; D.w = d_quad + 2 * I.Mpad;
   D.tri_nbr = d_nbr; D.tri_geo = d_geo;
+  D.tri_geo2 = d_geo2; D.tri_lg = d_lg;
   D.st = I.st; D.partials = I.partials;
   D.kind = I.kind; D.order = order; D.integrator = integrator; D.storage = storage;
   D.nx = I.nx; D.ny = I.ny; D.M = I.M; D.Mpad = I.Mpad;
@@ -771,6 +799,8 @@ rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_ite
     cudaError_t e;
     if (kind == RT_MESH_CARTESIAN)
       e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, run, cvec, ly_max, stream, uni);
+    else if (order == 2)
+      e = launch_tri2_stage(d_desc, d_items, n_items, stages[i], storage, std::min(vec, 2), stream);
     else
       e = launch_tri_stage(d_desc, d_items, n_items, stages[i], storage, vec, stream);
     if (e != cudaSuccess) {

@@ -5,6 +5,7 @@
 //   mat, region   uint8 per cell (material id, QoI region id)
 //   quad          float xi[Mpad], eta[Mpad], w[Mpad] (padding: xi = eta = w = 0)
 //   tri_nbr/geo   triangles only: neighbours and (n*l)/A per local edge
+//   tri_geo2/lg   triangles, second order: reconstruction vectors, limited gradient
 //   desc          InstDesc (tensor maps, pointers, constants)
 //   state         InstState (step, buffer parity, status, FP64 QoI sums)
 //   partials      FP64 per-work-item QoI partial sums [n_items][NQ]
@@ -64,7 +65,8 @@ struct alignas(128) InstDesc {
   const float* eta;
   const float* w;
   const int4* tri_nbr;          // {nbr0, nbr1, nbr2, mat | region << 8}; nbr < 0: -1 - side
-  const float4* tri_geo;        // 2 per cell: {ax0, ay0, ax1, ay1}, {ax2, ay2, area, 0}; a = (n*l)/A
+  const float4* tri_geo;        // 2 per cell: {ax0, ay0, ax1, ay1}, {ax2, ay2, area, eps^2}; a = (n*l)/A,
+                                // eps = A^3 (the second-order limiter's, Sec. 4.2)
   InstState* st;
   double* partials;             // [n_items][NQ]
 
@@ -94,7 +96,12 @@ struct alignas(128) InstDesc {
   // normal)
   const int4* box_tasks;
   double* box_partials;         // [n_box_items][2 * kMaxBox]
-  int32_t n_boxes, n_box_tasks;
+  int32_t n_boxes, n_box_tasks;  // triangles, second order: per cell {r0x, r0y, r1x, r1y}, {r2x, r2y, d0x, d0y},
+  // {d1x, d1y, d2x, d2y} (r_e: centroid to edge midpoint; d_e: centroid to the
+  // neighbour's centroid, 0 on the boundary), and the limited gradient L g,
+  // FP32 [cell][2][Mpad] (x row, then y row)
+  const float4* tri_geo2;
+  float* tri_lg;
 };
 
 struct WorkItem {
@@ -121,6 +128,10 @@ cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, in
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
+// Second-order triangle stage: the limited-gradient kernel, then the stage kernel
+// (vec 1 or 2).
+cudaError_t launch_tri2_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
+                              int storage, int vec, cudaStream_t stream);
 // Outflow through the QoI boxes after a time step (stage = STAGE_EULER, or
 // STAGE_HEUN2 after a whole Heun step) with the step's time-integration
 // update, or of the current state (STAGE_INIT). Work items: a = first face,

@@ -121,9 +121,9 @@ def test_create_rejects_bad_cells_and_meshes(rt):
     with pytest.raises(rt.RTError) as e:
         _create(rt, t, quad)
     assert e.value.code == rt.RT_EINVAL
-    # MUSCL is Cartesian only
+    # second order on triangles: still validated (order 3 rejected)
     with pytest.raises(rt.RTError) as e:
-        _create(rt, si.enclosure_problem(6), quad, order=2)
+        _create(rt, si.enclosure_problem(6), quad, order=3)
     assert e.value.code == rt.RT_EINVAL
 
 

@@ -332,6 +332,66 @@ def test_dp2_materials_on_triangles(rt):
 
 
 # ------------------------------------------------------------------ triangles
+# second order on triangles (Sec. 4.2): Green-Gauss gradient + Venkatakrishnan limiter
+@pytest.mark.parametrize("integrator", ["euler", "heun"])
+@pytest.mark.parametrize("n_p,n_phi", [(2, 16), (4, 16), (8, 16)])
+def test_triangles_second_order_random_state(rt, integrator, n_p, n_phi):
+    """Jittered enclosure mesh (2 * 26^2 triangles) from a random state, so the
+    gradient, the limiter (extrema everywhere) and the reconstructed traces act
+    on every cell and ordinate; 32, 64 and 128 ordinates (1 and 2 per lane)."""
+    p = si.enclosure_problem(26, jitter=0.2, seed=1)
+    integ = rt.RT_EULER if integrator == "euler" else rt.RT_HEUN
+    psi0 = si.random_psi(p.mesh.n_cells, n_p * n_phi, seed=8)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, n_p, n_phi, 2, integ, 6, psi0=psi0)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 4, scale=S["mass"] + sum(acc.abs_int))
+
+
+def test_triangles_second_order_enclosure_and_lattice(rt):
+    """From psi = 0: the enclosure with its inflow (Heun, 40 steps) and the
+    lattice on a jittered triangle mesh, against the oracle; the particle
+    balance closes."""
+    p = si.enclosure_problem(30, jitter=0.2, seed=0)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, p, 4, 16, 2, rt.RT_HEUN, 40)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 4, scale=S["mass"] + sum(acc.abs_int))
+    bal = q["mass"] + sum(q["abs_int"]) + q["outflow_int"]
+    assert abs(bal) <= 1e-5 * (q["mass"] + sum(q["abs_int"]))
+    t = si.lattice_triangle_problem(21, jitter=0.2, seed=3, t_end=0.8)
+    psi, phi, q, ref, acc, S, op, info = run_pair(rt, t, 4, 16, 2, rt.RT_HEUN, 12)
+    assert rel_l2(psi, ref) <= PSI_TOL
+    check_qoi(q, acc, S, 3, scale=S["mass"])
+
+
+def test_triangles_second_order_bf16_and_batch(rt):
+    """BF16 storage stays within the measured bound of FP32 storage, and a
+    second-order triangle problem batched with a first-order one and a
+    Cartesian one equals the same problems alone, bit for bit."""
+    p = si.enclosure_problem(30, jitter=0.2, seed=0, t_end=0.6)
+    quad = rt.rt_quad_product(4, 16)
+    outs = {}
+    for storage in (0, 1):
+        s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, storage=storage)
+        s.step()
+        outs[storage] = (s.psi(), s.qoi())
+        s.close()
+    assert rel_l2(outs[1][0], outs[0][0]) < 3e-2
+    probs = [p, si.enclosure_problem(20, jitter=0.2, seed=4, t_end=0.6), si.lattice_problem(28, t_end=0.6)]
+    orders = [2, 1, 2]
+    quads = [quad, rt.rt_quad_product(2, 16), rt.rt_quad_product(4, 16)]
+    b = rt.Batch(probs, quads, orders=orders, integrators=[rt.RT_HEUN] * 3)
+    b.run()
+    for i, (pr, qd, od) in enumerate(zip(probs, quads, orders)):
+        s = rt.Solver(pr, qd, order=od, integrator=rt.RT_HEUN)
+        s.step()
+        a, c = b.qoi(i), s.qoi()
+        assert np.array_equal(b.psi(i), s.psi()), i
+        s.close()
+        for k in ("mass", "abs_int", "outflow_int"):
+            assert np.array_equal(np.asarray(a[k]), np.asarray(c[k])), (i, k)
+    b.close()
+
+
 @pytest.mark.parametrize("integrator", ["euler", "heun"])
 def test_enclosure_triangles(rt, integrator):
     """Jittered split-square enclosure mesh (2*40^2 triangles), 4x16 ordinates."""
