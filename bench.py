@@ -267,7 +267,6 @@ def run_ours(args, spec):
     updates = dof * K * world
     value = updates / (ms * 1e-3)
     bpu = bytes_per_update(order, integ, storage, mesh)
-    # each stage launch is followed by the QoI-box launch when the problem has boxes
     # stage launches, plus one QoI-box launch per step (Cartesian problems with
     # boxes); second order on triangles runs a gradient launch before each stage
     launches_per_step = info.stages_per_step * (2 if (mesh != "lattice" and order == 2) else 1) + \
