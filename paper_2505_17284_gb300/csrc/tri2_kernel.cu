@@ -10,7 +10,8 @@
 //
 // Two kernels per stage, both persistent over 64-cell chunks like the
 // first-order stage kernel (chunk metadata staged in shared memory by bulk
-// copies, one warp per cell, lanes over ordinates):
+// copies, one warp per cell, lanes over ordinates; 3 CTAs per SM, so the
+// 3-per-SM persistent grid is resident at once):
 //   tri_grad_kernel    reads psi of a cell and its three neighbours and writes
 //                      the limited gradient L g (two FP32 rows per cell);
 //   tri_stage2_kernel  reads psi and L g of a cell and its neighbours, takes
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kT2Threads, 3)
 
 // -------------------------------------------------------------------- stage
 template <int VEC, int STAGE, typename T>
-__global__ void __launch_bounds__(kT2Threads, 2)
+__global__ void __launch_bounds__(kT2Threads, 3)
     tri_stage2_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
   __shared__ __align__(16) T2Meta meta;
   __shared__ double red[(kT2Warps + 1) * NQ];
