@@ -800,7 +800,7 @@ rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_ite
     if (kind == RT_MESH_CARTESIAN)
       e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, run, cvec, ly_max, stream, uni);
     else if (order == 2)
-      e = launch_tri2_stage(d_desc, d_items, n_items, stages[i], storage, std::min(vec, 2), stream);
+      e = launch_tri2_stage(d_desc, d_items, n_items, stages[i], storage, std::min(vec, 2), vec, stream);
     else
       e = launch_tri_stage(d_desc, d_items, n_items, stages[i], storage, vec, stream);
     if (e != cudaSuccess) {

@@ -128,10 +128,10 @@ cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, in
                              int storage, int vec, cudaStream_t stream);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
-// Second-order triangle stage: the limited-gradient kernel, then the stage kernel
-// (vec 1 or 2).
+// Second-order triangle stage: the limited-gradient kernel (grad_vec ordinates
+// per lane: 1, 2 or 4), then the stage kernel (vec 1 or 2).
 cudaError_t launch_tri2_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
-                              int storage, int vec, cudaStream_t stream);
+                              int storage, int vec, int grad_vec, cudaStream_t stream);
 // Outflow through the QoI boxes after a time step (stage = STAGE_EULER, or
 // STAGE_HEUN2 after a whole Heun step) with the step's time-integration
 // update, or of the current state (STAGE_INIT). Work items: a = first face,

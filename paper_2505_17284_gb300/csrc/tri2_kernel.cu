@@ -383,11 +383,14 @@ __global__ void __launch_bounds__(kT2Threads, 3)
 }  // namespace
 
 cudaError_t launch_tri2_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage, int storage,
-                              int vec, cudaStream_t s) {
+                              int vec, int grad_vec, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
+  // the gradient pass takes 4 ordinates per lane where the quadrature allows
+  // (fewer, wider loads); the stage pass at most 2 (its registers)
 #define RTK_T2(V, ST, TT)                                                                       \
   if (vec == V && stage == ST) {                                                                \
-    tri_grad_kernel<V, TT><<<n_items, kT2Threads, 0, s>>>(d_desc, d_items, ST);                 \
+    if (grad_vec == 4) tri_grad_kernel<4, TT><<<n_items, kT2Threads, 0, s>>>(d_desc, d_items, ST); \
+    else tri_grad_kernel<V, TT><<<n_items, kT2Threads, 0, s>>>(d_desc, d_items, ST);            \
     cudaError_t e = cudaGetLastError();                                                         \
     if (e != cudaSuccess) return e;                                                             \
     tri_stage2_kernel<V, ST, TT><<<n_items, kT2Threads, 0, s>>>(d_desc, d_items);               \
