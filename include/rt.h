@@ -276,7 +276,10 @@ rt_status rt_set_psi(rt_solver* s, const double* host, int64_t n);
 
 /* Device view of the current state: psi (storage type, [cell][M_pad], ordinates
  * in the internal order: the caller's unless rt_info_t.regrouped) and phi
- * (float, [cell]). Pointers stay owned by the solver and are valid until the
+ * (float, [cell]). Triangle meshes keep their cells in an internal order (the
+ * Morton order of the centroids, ties by the caller's index); Cartesian meshes
+ * in the caller's. rt_get_psi, rt_set_psi and rt_get_phi always use the
+ * caller's orders. Pointers stay owned by the solver and are valid until the
  * next rt_step (Euler alternates two buffers) or rt_destroy. */
 rt_status rt_device_state(rt_solver* s, void** psi, void** phi, int32_t* storage);
 

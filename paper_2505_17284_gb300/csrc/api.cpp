@@ -246,7 +246,11 @@ rt_status rt_get_phi(rt_solver* s, double* host, int64_t n) {
     set_error("reading phi failed: %s", cudaGetErrorString(e));
     return fail(s, RT_ECUDA);
   }
-  for (int64_t i = 0; i < I.n_cells; ++i) host[i] = tmp[i];
+  if (I.cell_perm.empty()) {
+    for (int64_t i = 0; i < I.n_cells; ++i) host[i] = tmp[i];
+  } else {
+    for (int64_t i = 0; i < I.n_cells; ++i) host[I.cell_perm[i]] = tmp[i];
+  }
   return RT_OK;
 }
 

@@ -263,6 +263,66 @@ static rt_status triangle_metadata(const rt_mesh* m, const int32_t* cell_mat, co
   return RT_OK;
 }
 
+// Device order of the triangles: Morton (Z-order) of the centroids on a
+// 2^16 x 2^16 grid over the bounding box, ties by the caller's index. Cells that
+// share an edge are then mostly close in the order, so the neighbour rows a
+// kernel gathers were read recently by the CTAs working next to it (the caller's
+// order may put a neighbour a whole grid row away). perm[new] = caller's index;
+// the device arrays of tm (neighbours, geometry) are rewritten in that order
+// with neighbour ids renumbered; tm.area stays in the caller's order.
+static void reorder_triangles(const rt_mesh* m, TriMeta& tm, std::vector<int32_t>& perm) {
+  const int64_t nt = m->n_tri;
+  const double* V = m->vxy;
+  const int32_t* T = m->tri;
+  double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+  std::vector<double> cx(nt), cy(nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    cx[t] = (V[2 * T[3 * t]] + V[2 * T[3 * t + 1]] + V[2 * T[3 * t + 2]]) / 3.0;
+    cy[t] = (V[2 * T[3 * t] + 1] + V[2 * T[3 * t + 1] + 1] + V[2 * T[3 * t + 2] + 1]) / 3.0;
+    xmin = std::min(xmin, cx[t]); xmax = std::max(xmax, cx[t]);
+    ymin = std::min(ymin, cy[t]); ymax = std::max(ymax, cy[t]);
+  }
+  const double sx = xmax > xmin ? 65535.0 / (xmax - xmin) : 0.0, sy = ymax > ymin ? 65535.0 / (ymax - ymin) : 0.0;
+  auto spread = [](uint32_t v) {   // bit i of v to bit 2i
+    uint64_t x = v & 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+  };
+  std::vector<uint64_t> key(nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    const uint32_t ix = (uint32_t)std::min(65535.0, std::max(0.0, (cx[t] - xmin) * sx));
+    const uint32_t iy = (uint32_t)std::min(65535.0, std::max(0.0, (cy[t] - ymin) * sy));
+    key[t] = (spread(ix) | (spread(iy) << 1)) << 31 | (uint64_t)t;   // ties by the caller's index
+  }
+  std::vector<uint64_t> order(key);
+  std::sort(order.begin(), order.end());
+  perm.resize(nt);
+  std::vector<int32_t> rank(nt);
+  for (int64_t i = 0; i < nt; ++i) {
+    perm[i] = (int32_t)(order[i] & 0x7fffffffu);
+    rank[perm[i]] = (int32_t)i;
+  }
+  std::vector<int4> nbr(nt);
+  std::vector<float4> geo(2 * nt), geo2(3 * nt);
+  for (int64_t i = 0; i < nt; ++i) {
+    const int64_t t = perm[i];
+    int4 r = tm.nbr[t];
+    r.x = r.x >= 0 ? rank[r.x] : r.x;
+    r.y = r.y >= 0 ? rank[r.y] : r.y;
+    r.z = r.z >= 0 ? rank[r.z] : r.z;
+    nbr[i] = r;
+    geo[2 * i] = tm.geo[2 * t];
+    geo[2 * i + 1] = tm.geo[2 * t + 1];
+    for (int j = 0; j < 3; ++j) geo2[3 * i + j] = tm.geo2[3 * t + j];
+  }
+  tm.nbr.swap(nbr);
+  tm.geo.swap(geo);
+  tm.geo2.swap(geo2);
+}
+
 // ---------------------------------------------------------------- tiles
 // Ordinates per lane: the largest V in {4, 2, 1} that divides M_pad/32 and for
 // which every group of V consecutive ordinates has one sign of xi (zero-weight
@@ -514,6 +574,7 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   if (I.kind == RT_MESH_TRIANGLES) {
     s = triangle_metadata(mesh, mat->cell_mat, mat->cell_region, tm);
     if (s != RT_OK) return s;
+    reorder_triangles(mesh, tm, I.cell_perm);
   }
 
   // --- time step (Sec. 4.3: uniform dt = T / N_t)
@@ -891,12 +952,20 @@ rt_status copy_psi_out(const Instance& I, DeviceArena& arena, cudaStream_t strea
   void* tmp = nullptr;
   rt_status st = arena.get((size_t)chunk * I.M * 8, &tmp);
   if (st != RT_OK) return st;
+  // cells in device order; with a cell permutation each chunk is staged on the
+  // host and its rows scattered to the caller's order
+  const bool perm = !I.cell_perm.empty();
+  std::vector<double> stage(perm ? (size_t)chunk * I.M : 0);
   for (int64_t c0 = 0; c0 < I.n_cells; c0 += chunk) {
     const int64_t nc = std::min(chunk, I.n_cells - c0);
     const char* src = (const char*)I.psi[buf] + (size_t)c0 * I.Mpad * es;
     cudaError_t e = launch_convert_out(src, (double*)tmp, nc, I.M, I.Mpad, I.storage, I.kmap, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host + c0 * I.M, tmp, (size_t)nc * I.M * 8, cudaMemcpyDeviceToHost, stream);
+    double* out = perm ? stage.data() : host + c0 * I.M;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)nc * I.M * 8, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess && perm)
+      for (int64_t i = 0; i < nc; ++i)
+        std::memcpy(host + (int64_t)I.cell_perm[c0 + i] * I.M, stage.data() + i * I.M, (size_t)I.M * 8);
     if (e != cudaSuccess) {
       arena.release(tmp);
       set_error("reading psi failed: %s", cudaGetErrorString(e));
@@ -913,10 +982,16 @@ rt_status copy_psi_in(const Instance& I, DeviceArena& arena, cudaStream_t stream
   void* tmp = nullptr;
   rt_status st = arena.get((size_t)chunk * I.M * 8, &tmp);
   if (st != RT_OK) return st;
+  const bool perm = !I.cell_perm.empty();
+  std::vector<double> stage(perm ? (size_t)chunk * I.M : 0);
   for (int64_t c0 = 0; c0 < I.n_cells; c0 += chunk) {
     const int64_t nc = std::min(chunk, I.n_cells - c0);
     char* dst = (char*)I.psi[buf] + (size_t)c0 * I.Mpad * es;
-    cudaError_t e = cudaMemcpyAsync(tmp, host + c0 * I.M, (size_t)nc * I.M * 8, cudaMemcpyHostToDevice, stream);
+    if (perm)
+      for (int64_t i = 0; i < nc; ++i)
+        std::memcpy(stage.data() + i * I.M, host + (int64_t)I.cell_perm[c0 + i] * I.M, (size_t)I.M * 8);
+    const double* in = perm ? stage.data() : host + c0 * I.M;
+    cudaError_t e = cudaMemcpyAsync(tmp, in, (size_t)nc * I.M * 8, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = launch_convert_in((const double*)tmp, dst, nc, I.M, I.Mpad, I.storage, I.inv, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {

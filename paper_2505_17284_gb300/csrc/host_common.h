@@ -56,6 +56,9 @@ struct Instance {
   int32_t regrouped = 0;
   int32_t* kmap = nullptr;
   int32_t* inv = nullptr;
+  // triangles: device order of the cells (cell_perm[device index] = caller's
+  // index; empty: the caller's order)
+  std::vector<int32_t> cell_perm;
   int32_t n_regions = 0;
   double source_rate = 0;   // 2 pi sum_i A_i Q_i
   size_t cart_smem = 0;
