@@ -207,15 +207,41 @@ print(json.dumps({"rate": p.mesh.n_cells * MQ * steps / (t1 - t0), "n": n2, "ste
     return d["rate"], desc, d["seconds"]
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+# Under torchrun every rank solves its own copy of the workload (no data-path
+# collective: one solve does not shard across GPUs); the job's time is the
+# slowest rank's and its throughput the units of all ranks over that time.
+def replica_env():
+    """(rank, world size, local rank) from the torchrun environment."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, device):
+    """The largest x over all ranks of the default process group (x itself
+    when there is none)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (ms)."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, spec):
     import numpy as np
     import torch
     from paper_2505_17284_gb300 import build as B, rt
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replica_env()
     dist = world > 1
     if dist:
         import torch.distributed as tdist
@@ -259,13 +285,9 @@ def run_ours(args, spec):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     q = solver.qoi()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
     dof = info.n_cells * info.M
-    updates = dof * K * world
-    value = updates / (ms * 1e-3)
+    value = job_value(dof * K, world, ms)
     bpu = bytes_per_update(order, integ, storage, mesh)
     # stage launches, plus one QoI-box launch per step (Cartesian problems with
     # boxes); second order on triangles runs a gradient launch before each stage
@@ -346,9 +368,9 @@ def run_ours(args, spec):
 
 
 def run_reference(args, spec):
-    rank = int(os.environ.get("RANK", "0"))
+    rank, _, _ = replica_env()
     if rank != 0:
-        return
+        return   # the oracle runs on rank 0 alone; the other ranks exit without work
     K, W = args.steps, args.warmup
     per_step = max(0.5, min(20.0, 150.0 / (K + W)))
     import numpy as np
@@ -580,7 +602,7 @@ def run_serve(args, w):
     print(json.dumps(out))
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -592,9 +614,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="Cartesian tiles from the library's model, not the autotuner")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    return args
+
+
+def main():
+    args = parse_args()
     if args.workload in EXTRA_WORKLOADS:
         w = EXTRA_WORKLOADS[args.workload]
         if args.impl == "reference":
