@@ -267,6 +267,13 @@ rt_status rt_info(const rt_solver* s, rt_info_t* out);
 /* Copy psi (n = n_cells*M doubles, [cell][k]) or phi (n = n_cells doubles) of the
  * current state to host memory; synchronises. RT_EINVAL if n is wrong. */
 rt_status rt_get_psi(rt_solver* s, double* host, int64_t n);
+
+/* Copy psi of n selected cells (caller's cell ids in cells[0..n), any order,
+ * repeats allowed) to host[n][M] doubles, ordinates in the caller's order;
+ * synchronises. For probing a large state without copying all of it (a
+ * 1400^2 x 512 lattice holds 8 GB as doubles). RT_EINVAL if n < 0, a pointer
+ * is NULL (with n > 0) or a cell id is out of range (nothing copied then). */
+rt_status rt_get_psi_cells(rt_solver* s, const int64_t* cells, int64_t n, double* host);
 rt_status rt_get_phi(rt_solver* s, double* host, int64_t n);
 
 /* Replace the current state by psi (n = n_cells*M doubles, [cell][k]); rounds to

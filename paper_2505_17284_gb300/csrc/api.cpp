@@ -230,6 +230,17 @@ rt_status rt_get_psi(rt_solver* s, double* host, int64_t n) {
   return st == RT_OK ? RT_OK : fail(s, st);
 }
 
+rt_status rt_get_psi_cells(rt_solver* s, const int64_t* cells, int64_t n, double* host) {
+  clear_error();
+  if (!s || n < 0 || (n > 0 && (!cells || !host))) { set_error("solver, cells and host are required (n >= 0)"); return RT_EINVAL; }
+  if (s->failed) { set_error("solver is in its error state"); return RT_ESTATE; }
+  int buf = 0;
+  rt_status st = current_buffers(s, &buf);
+  if (st != RT_OK) return st;
+  st = copy_psi_cells_out(s->I, s->arena, s->stream, buf, cells, n, host);
+  return (st == RT_OK || st == RT_EINVAL) ? st : fail(s, st);
+}
+
 rt_status rt_get_phi(rt_solver* s, double* host, int64_t n) {
   clear_error();
   if (!s || !host) { set_error("solver and host are required"); return RT_EINVAL; }

@@ -1004,4 +1004,42 @@ rt_status copy_psi_in(const Instance& I, DeviceArena& arena, cudaStream_t stream
   return RT_OK;
 }
 
+rt_status copy_psi_cells_out(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf,
+                             const int64_t* cells, int64_t n, double* host) {
+  if (n == 0) return RT_OK;
+  // device index of each caller's cell
+  std::vector<int64_t> dev((size_t)n);
+  std::vector<int32_t> rank;
+  if (!I.cell_perm.empty()) {
+    rank.resize(I.cell_perm.size());
+    for (size_t i = 0; i < I.cell_perm.size(); ++i) rank[I.cell_perm[i]] = (int32_t)i;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (cells[i] < 0 || cells[i] >= I.n_cells) { set_error("cell id %lld out of range", (long long)cells[i]); return RT_EINVAL; }
+    dev[i] = rank.empty() ? cells[i] : rank[cells[i]];
+  }
+  const size_t es = I.storage == RT_BF16 ? 2 : 4;
+  const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(n, (16LL << 20) / (8LL * I.M)));
+  void* tmp = nullptr;
+  rt_status st = arena.get((size_t)batch * I.M * 8, &tmp);
+  if (st != RT_OK) return st;
+  for (int64_t c0 = 0; c0 < n; c0 += batch) {
+    const int64_t nc = std::min(batch, n - c0);
+    cudaError_t e = cudaSuccess;
+    for (int64_t i = 0; i < nc && e == cudaSuccess; ++i) {
+      const char* src = (const char*)I.psi[buf] + (size_t)dev[c0 + i] * I.Mpad * es;
+      e = launch_convert_out(src, (double*)tmp + i * I.M, 1, I.M, I.Mpad, I.storage, I.kmap, stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host + c0 * I.M, tmp, (size_t)nc * I.M * 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      arena.release(tmp);
+      set_error("reading psi of cells failed: %s", cudaGetErrorString(e));
+      return RT_ECUDA;
+    }
+  }
+  arena.release(tmp);
+  return RT_OK;
+}
+
 }  // namespace rtk

@@ -104,5 +104,8 @@ void fill_qoi(const Instance& I, const InstState& h, rt_qoi_t* out);
 // Copy psi of buffer `buf` to host doubles [cell][M] through a bounded device buffer.
 rt_status copy_psi_out(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf, double* host);
 rt_status copy_psi_in(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf, const double* host);
+// Copy psi of the given caller's cells of buffer `buf` to host doubles [n][M].
+rt_status copy_psi_cells_out(const Instance& I, DeviceArena& arena, cudaStream_t stream, int buf,
+                             const int64_t* cells, int64_t n, double* host);
 
 }  // namespace rtk

@@ -117,6 +117,7 @@ SIGNATURES = {
     "rt_qoi": (C.c_int, [C.c_void_p, C.POINTER(rt_qoi_t)]),
     "rt_info": (C.c_int, [C.c_void_p, C.POINTER(rt_info_t)]),
     "rt_get_psi": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
+    "rt_get_psi_cells": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_int64, _dp]),
     "rt_get_phi": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
     "rt_set_psi": (C.c_int, [C.c_void_p, _dp, C.c_int64]),
     "rt_device_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]),
@@ -218,6 +219,13 @@ def rt_info(h) -> rt_info_t:
 def rt_get_psi(h, n_cells: int, M: int) -> np.ndarray:
     out = np.empty((n_cells, M))
     check(_fns().rt_get_psi(h, _ptr(out), out.size))
+    return out
+
+
+def rt_get_psi_cells(h, cells, M: int) -> np.ndarray:
+    idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+    out = np.empty((idx.size, M))
+    check(_fns().rt_get_psi_cells(h, idx.ctypes.data_as(C.POINTER(C.c_int64)), idx.size, _ptr(out)))
     return out
 
 
@@ -426,6 +434,10 @@ class Solver:
 
     def psi(self) -> np.ndarray:
         return rt_get_psi(self.h, self.n_cells, self.M)
+
+    def psi_cells(self, cells) -> np.ndarray:
+        """psi of the given cells ([n, M], caller's orders) without copying the whole state."""
+        return rt_get_psi_cells(self.h, cells, self.M)
 
     def phi(self) -> np.ndarray:
         return rt_get_phi(self.h, self.n_cells)

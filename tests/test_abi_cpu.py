@@ -165,3 +165,8 @@ def test_qoi_struct_layout(rt):
     # the header's rt_qoi_t: 392 bytes, box entries last
     assert C.sizeof(rt.rt_qoi_t) == 392
     assert rt.rt_qoi_t.box_out_int.offset == 392 - 8 * rt.RT_MAX_BOXES
+
+
+def test_get_psi_cells_rejects_bad_arguments(rt):
+    lib = rt.load_library()
+    assert lib.rt_get_psi_cells(None, None, 0, None) == rt.RT_EINVAL
