@@ -1,12 +1,14 @@
 """GPU parity at the production sizes, in the launch configuration the bench
 times: the lattice at 1400^2 x 512 ordinates (MUSCL, Heun, FP32, autotuned
 tiles, QoI squares attached) and the enclosure at 1300^2 split (3.38e6
-triangles) x 256 ordinates (first order, Euler, FP32).
+triangles) x 256 ordinates (first order, Euler, FP32; and the paper's second
+order scheme with Heun).
 
 The whole state is too large for the oracle, so sampled cells are checked one
 by one: the value of a cell after K steps depends only on the cells within the
 scheme's domain of dependence (4 cells per Heun step with MUSCL, one triangle
-per Euler step at first order), so the oracle solves a patch around the cell,
+per Euler step at first order, four per Heun step at second order on
+triangles), so the oracle solves a patch around the cell,
 wide enough that its artificial edges cannot reach the centre in K steps, from
 the same initial state (psi = 0) with the same dt. Properties that hold at any
 size are checked on the whole state: the particle balance and, for the
@@ -139,5 +141,35 @@ def test_enclosure_1300_production_sampled_parity(rt):
     assert np.max(np.abs(gpu - ref)) <= 10 * PSI_TOL * scale
     assert np.all(gpu[-12:] == 0.0)
     # whole state: particle balance (no source: mass + absorbed + outflow = 0)
+    bal = q["mass"] + sum(q["abs_int"]) + q["outflow_int"]
+    assert abs(bal) <= 1e-5 * (q["mass"] + sum(q["abs_int"]))
+
+
+def test_enclosure_1300_second_order_sampled_parity(rt):
+    """The paper's production scheme (Green-Gauss + Venkatakrishnan, Heun) at
+    1300^2 split x 256: each stage reaches two triangles, so a step reaches
+    four and the patch has half-width 4K + 2 squares."""
+    n, K = 1300, 3
+    p = si.enclosure_problem(n, jitter=0.2, seed=0)
+    s = rt.Solver(p, rt.rt_quad_product(8, 32), order=2, integrator=rt.RT_HEUN)
+    s.step(K)
+    info, q = s.info, s.qoi()
+    rng = np.random.default_rng(11)
+    near = np.stack([rng.integers(0, 6, size=16), rng.integers(400, 693, size=16)], axis=1)
+    far = np.stack([rng.integers(200, n, size=4), rng.integers(0, n, size=4)], axis=1)
+    sq_ij = np.concatenate([near, far])
+    cells = np.concatenate([[2 * (j * n + i), 2 * (j * n + i) + 1] for i, j in sq_ij])
+    gpu = s.psi_cells(cells)
+    s.close()
+    quad = oracle.product_quadrature(8, 32)
+    ref = np.empty_like(gpu)
+    for r, (ci, cj) in enumerate(sq_ij):
+        pp, (c0, c1) = triangle_patch(p, n, int(ci), int(cj), 4 * K + 2)
+        op = oracle.TriangleOracle(pp, quad, order=2)
+        psi, _, _ = oracle.run(op, np.zeros((pp.mesh.n_cells, 256)), info.dt, K, "heun")
+        ref[2 * r], ref[2 * r + 1] = psi[c0], psi[c1]
+    assert np.abs(ref).max() > 0
+    assert float(np.linalg.norm(gpu - ref) / np.linalg.norm(ref)) <= PSI_TOL
+    assert np.all(gpu[-8:] == 0.0)
     bal = q["mass"] + sum(q["abs_int"]) + q["outflow_int"]
     assert abs(bal) <= 1e-5 * (q["mass"] + sum(q["abs_int"]))

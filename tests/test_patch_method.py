@@ -36,3 +36,18 @@ def test_triangle_patch_equals_whole_domain():
         t0 = 2 * (cj * n + ci)
         assert np.array_equal(ps[c0], full[t0]) and np.array_equal(ps[c1], full[t0 + 1]), (ci, cj)
     assert np.abs(full).max() > 0
+
+
+def test_second_order_triangle_patch_equals_whole_domain():
+    n, K = 130, 3
+    p = si.enclosure_problem(n, jitter=0.2, seed=0)
+    q = oracle.product_quadrature(2, 8)
+    op = oracle.TriangleOracle(p, q, order=2)
+    _, dt = oracle.triangle_dt(op, p.t_end)
+    full, _, _ = oracle.run(op, np.zeros((p.mesh.n_cells, 16)), dt, K, "heun")
+    for ci, cj in [(0, 50), (2, 60), (5, 45), (1, 85)]:
+        pp, (c0, c1) = triangle_patch(p, n, ci, cj, 4 * K + 2)
+        ps, _, _ = oracle.run(oracle.TriangleOracle(pp, q, order=2), np.zeros((pp.mesh.n_cells, 16)), dt, K, "heun")
+        t0 = 2 * (cj * n + ci)
+        assert np.array_equal(ps[c0], full[t0]) and np.array_equal(ps[c1], full[t0 + 1]), (ci, cj)
+    assert np.abs(full).max() > 0
