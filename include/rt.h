@@ -216,8 +216,8 @@ typedef struct {
                         caller's order does not give sign-uniform chunks and the padding adds at most
                         1/8; M_pad is then the padded count). rt_get_psi / rt_set_psi always use the
                         caller's order; rt_device_state exposes the internal one. */
-  int32_t n_box_items; /* QoI boxes: work items of the box-outflow launch that follows each stage
-                          (0: no boxes, no such launch) */
+  int32_t n_box_items; /* QoI boxes: work items of the box-outflow launch that follows each time
+                          step's last stage (0: no boxes, no such launch) */
 } rt_info_t;
 
 typedef struct rt_solver rt_solver;
@@ -253,7 +253,9 @@ rt_status rt_create(const rt_mesh* mesh, const rt_materials* mat, const rt_quadr
                     const rt_boundary* bc, const rt_options* opts, rt_solver** out);
 
 /* Enqueue n time steps (clamped at N_t) on the solver's stream; returns after
- * enqueueing. Each step is one launch (Euler) or two (Heun stages). */
+ * enqueueing. Each step is one launch (Euler) or two (Heun stages); second order
+ * on triangles adds a gradient launch before each stage, and QoI boxes one
+ * launch after the step's last stage. */
 rt_status rt_step(rt_solver* s, int64_t n);
 
 /* Synchronise the stream and copy the QoIs to *out (392 bytes). Returns
