@@ -470,7 +470,7 @@ def run_sweep(args, w):
         shapes.setdefault((j.problem.mesh.nx, j.M), j)
     for j in shapes.values():
         autotune.tuned_config(j.problem, j.quad, j.order, j.integrator, rt.RT_FP32, j.dt, steps=3)
-    best_ty, ty_times = S.tune_batch(jobs, candidates=(0, 24, 48, 96), steps=3)
+    best_ty, ty_times = S.tune_batch(jobs, candidates=(0, 16, 24, 32, 48, 96), steps=3)
     clocks = ClockSampler(0)
     clocks.start()
     phases = {}
