@@ -588,6 +588,25 @@ def test_set_psi_roundtrip_and_device_view(rt):
     s.close()
 
 
+def test_psi_cells_equals_rows_of_the_whole_state(rt):
+    """rt_get_psi_cells returns the caller's rows on both mesh kinds (triangles
+    are stored in a different order on the device), for repeated and unsorted
+    ids; an id out of range is rejected and changes nothing."""
+    for p, order in ((si.lattice_problem(28, t_end=0.3), 2), (si.enclosure_problem(12, t_end=0.3), 2)):
+        s = rt.Solver(p, rt.rt_quad_product(2, 16), order=order, integrator=rt.RT_HEUN)
+        s.set_psi(si.random_psi(p.mesh.n_cells, 32, seed=2))
+        s.step(3)
+        full = s.psi()
+        cells = np.array([5, 0, p.mesh.n_cells - 1, 5, 17, 3])
+        assert np.array_equal(s.psi_cells(cells), full[cells])
+        assert s.psi_cells(np.array([], dtype=np.int64)).shape == (0, 32)
+        with pytest.raises(rt.RTError) as e:
+            s.psi_cells(np.array([0, p.mesh.n_cells]))
+        assert e.value.code == rt.RT_EINVAL
+        assert np.array_equal(s.psi(), full)
+        s.close()
+
+
 # ------------------------------------------------------------------ batches
 def test_batch_results_equal_single_solves_bitwise(rt):
     """Mixed grid sizes and ordinate counts in one batch: each problem's result is
