@@ -135,3 +135,11 @@ def test_tessellation_symmetry_and_moments():
         xi, eta, mu, w = oracle.tessellation_quadrature(N)
         err.append(abs((w * mu ** 4).sum() - 2 * np.pi / 5))
     assert 3.0 < err[0] / err[1] < 5.0 and 3.0 < err[1] / err[2] < 5.0
+
+
+def test_tessellation_order_22_has_the_papers_1936_angles():
+    """The paper's reference runs use the tessellation rule of order N = 22
+    with 1936 angles (Sec. 3.1, caption of the lattice figure): 4 N^2 = 1936."""
+    xi, eta, mu, w = oracle.tessellation_quadrature(22)
+    assert len(w) == 1936
+    assert abs(w.sum() - 2 * np.pi) < 1e-12
