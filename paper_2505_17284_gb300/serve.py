@@ -48,13 +48,17 @@ class Served:
         return self.finished - self.arrival
 
 
-def estimate_bytes(n_cells: int, M: int, storage=rt.RT_FP32, triangles=False) -> int:
+def estimate_bytes(n_cells: int, M: int, storage=rt.RT_FP32, triangles=False, order=1) -> int:
     """Upper estimate of a problem's device memory: two psi buffers (ordinates
     padded to 32), two phi buffers and per-cell metadata (larger for
-    triangles: neighbours, edge geometry, areas), plus fixed overhead."""
+    triangles: neighbours, edge geometry, areas), plus fixed overhead; second
+    order on triangles adds the limited gradient (two FP32 values per cell and
+    ordinate) and its reconstruction geometry."""
     es = 2 if storage == rt.RT_BF16 else 4
     Mpad = (M + 31) // 32 * 32
     per_cell = 2 * Mpad * es + 16 + (96 if triangles else 8)
+    if triangles and order == 2:
+        per_cell += 2 * Mpad * 4 + 48
     return int(n_cells * per_cell + (8 << 20))
 
 

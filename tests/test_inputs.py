@@ -114,3 +114,14 @@ def test_dp2_draws():
     u = si.uniform01(3, np.arange(100, 200, dtype=np.uint64))
     assert inst[1].sigma_a[2, 0] == 0.5 * u[2 + 2]
     assert inst[1].sigma_a[1, 1] == 5.0 + 10.0 * u[2 + 7 + 1]
+
+
+def test_serving_memory_estimate_covers_second_order_triangles():
+    """The admission estimate grows by the limited gradient (8 B per cell and
+    ordinate) for second-order triangle problems, and is exact in its psi term."""
+    from paper_2505_17284_gb300 import serve, rt
+    n, M = 1000, 100                       # M_pad = 128
+    base = serve.estimate_bytes(n, M, triangles=True)
+    two = serve.estimate_bytes(n, M, triangles=True, order=2)
+    assert two - base == n * (2 * 128 * 4 + 48)
+    assert serve.estimate_bytes(n, M) - serve.estimate_bytes(n, M, storage=rt.RT_BF16) == n * 2 * 128 * 2
