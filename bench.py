@@ -40,6 +40,7 @@ WORKLOADS = {
     "lattice70_o1_euler_fp32": ("lattice", 70, 4, 16, 1, "euler", "fp32", 0.5, 3.2),
     "lattice560_muscl_heun_fp32": ("lattice", 560, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
     "lattice840_muscl_heun_fp32": ("lattice", 840, 16, 32, 2, "heun", "fp32", 0.5, 3.2),
+    "lattice840_muscl_heun_bf16": ("lattice", 840, 16, 32, 2, "heun", "bf16", 0.5, 3.2),
     "enclosure650_tri_o1_euler_fp32": ("enclosure", 650, 8, 32, 1, "euler", "fp32", 0.0, 2.6),
     # the paper's production scheme on triangles: Green-Gauss + Venkatakrishnan, Heun
     "enclosure1300_tri_o2_heun_fp32": ("enclosure", 1300, 8, 32, 2, "heun", "fp32", 0.0, 2.6),

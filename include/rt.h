@@ -420,7 +420,10 @@ void rt_batch_destroy(rt_batch* b);
  *   nx, ny, dx, dy: Cartesian grid; M_pad: ordinates per cell in the psi layout
  *   [cell][M_pad] (a multiple of 32; padding ordinates must have xi = eta = w = 0);
  *   vec: ordinates per lane (1, 2 or 4; 0 means 1) - every group of vec
- *   consecutive ordinates must share the sign of xi; order 1 or 2; stage
+ *   consecutive ordinates must share the sign of xi (the kernel takes each
+ *   lane's upwind direction in x from the group's summed xi, so a group that
+ *   mixes signs gives wrong results, not an error, unless xi_host is given);
+ *   order 1 or 2; stage
  *   RT_STAGE_EULER / RT_STAGE_HEUN1 (psi_out = psi_in + dt F(psi_in)) or
  *   RT_STAGE_HEUN2 (psi_out = (psi_n + psi_in + dt F(psi_in))/2; psi_out may be
  *   psi_n); storage RT_FP32 or RT_BF16; tile_y rows per work item (0 = default);
@@ -430,7 +433,17 @@ void rt_batch_destroy(rt_batch* b);
  *   phi_out (float [cell]); cell_mat, cell_region (uint8 [cell]); xi, eta, w
  *   (float [M_pad]); qoi_out (double [n_regions + 2]: absorption per region,
  *   mass, boundary outflow of the output state); status_out (int32, optional:
- *   0, RT_ETIMEOUT or RT_ENONFINITE once the stream reaches it); stream.
+ *   0, RT_ETIMEOUT or RT_ENONFINITE once the stream reaches it; every call
+ *   starts from status 0, so a failed call does not carry over); stream;
+ *   step: index of the time step this stage belongs to (n for the stages that
+ *   advance psi^n; Heun's two stages share it). BF16 storage rounds
+ *   stochastically with random bits drawn from (element, step, stage), so
+ *   successive steps must pass successive indices: the same index on every
+ *   step would reuse the same bits and bias the rounding. With the indices of
+ *   rt_step (0, 1, 2, ...) the stored results match rt_step's. FP32 ignores it.
+ *   xi_host (host pointer, optional): a host copy of xi[0..M_pad); when given,
+ *   the call first checks that every group of vec consecutive ordinates
+ *   shares the sign of xi and returns RT_EINVAL if one does not.
  * Enqueues on `stream` and returns; RT_EINVAL on invalid arguments (nothing is
  * launched), RT_ECUDA if a launch fails. */
 #define RT_NOALLOC_MAX_WORK_ITEMS 8192
@@ -457,6 +470,8 @@ typedef struct {
   double* qoi_out;
   int32_t* status_out;
   void* stream;
+  int64_t step;
+  const float* xi_host;
 } rt_cart_stage_args;
 
 rt_status rt_cart_stage_noalloc(const rt_cart_stage_args* args);

@@ -33,6 +33,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -915,14 +916,25 @@ __global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
 
 template <int ORDER, int R, int V, int STAGE, typename T, bool UNI>
 static cudaError_t prepare_one(int ly_max) {
-  // raise the dynamic shared-memory limit of this kernel variant (idempotent)
-  static size_t s_limit = 0;
+  // Raise the dynamic shared-memory limit of this kernel variant. The attribute
+  // belongs to the current device, so the limit already raised is kept per
+  // device (atomics: callers on several host threads may race here; setting
+  // the attribute twice is harmless).
+  constexpr int kDev = 64;
+  static std::atomic<size_t> s_limit[kDev];
   const size_t smem = cart_smem_for<ORDER, R, V, STAGE, T>(ly_max);
-  if (smem > s_limit) {
-    cudaError_t e = cudaFuncSetAttribute(cart_stage_kernel<ORDER, R, V, STAGE, T, UNI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    s_limit = smem;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < kDev;
+  if (tracked && smem <= s_limit[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(cart_stage_kernel<ORDER, R, V, STAGE, T, UNI>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (tracked) {
+    size_t cur = s_limit[dev].load(std::memory_order_relaxed);
+    while (cur < smem && !s_limit[dev].compare_exchange_weak(cur, smem, std::memory_order_release)) {
+    }
   }
   return cudaSuccess;
 }

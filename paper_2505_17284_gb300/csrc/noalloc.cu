@@ -38,14 +38,19 @@ constexpr size_t kScratchBytes = kPartOff + (size_t)kMaxItems * NQ * sizeof(doub
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Write the descriptor and the work list into the scratch array and clear the
-// state block (ticket, status, step and parity must start at zero).
-__global__ void noalloc_setup_kernel(const __grid_constant__ InstDesc desc, int n_strips, int n_items) {
+// state block (ticket, status, parity and the QoI sums must start at zero),
+// then set the step counter to the caller's step index: the stage kernel draws
+// the stochastic-rounding bits of BF16 stores from it.
+__global__ void noalloc_setup_kernel(const __grid_constant__ InstDesc desc, int n_strips, int n_items,
+                                     int64_t step) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&desc);
   uint32_t* dst = reinterpret_cast<uint32_t*>(g_noalloc_scratch + kDescOff);
   for (int i = tid; i < (int)(sizeof(InstDesc) / 4); i += nt) dst[i] = src[i];
   uint32_t* stw = reinterpret_cast<uint32_t*>(g_noalloc_scratch + kStateOff);
   for (int i = tid; i < (int)(sizeof(InstState) / 4); i += nt) stw[i] = 0u;
+  __syncthreads();
+  if (tid == 0) reinterpret_cast<InstState*>(g_noalloc_scratch + kStateOff)->step = step;
   WorkItem* items = reinterpret_cast<WorkItem*>(g_noalloc_scratch + kItemsOff);
   for (int i = tid; i < n_items; i += nt) {
     WorkItem w;
@@ -176,6 +181,23 @@ extern "C" rt_status rt_cart_stage_noalloc(const rt_cart_stage_args* a) {
     set_error("psi buffers must be 16-byte aligned"); return RT_EINVAL;
   }
   if (a->psi_in == a->psi_out) { set_error("psi_out must not alias psi_in"); return RT_EINVAL; }
+  if (a->step < 0 || a->step == INT64_MAX) { set_error("step must be in [0, INT64_MAX)"); return RT_EINVAL; }
+  if (a->xi_host) {
+    // every group of vec consecutive ordinates must share the sign of xi
+    for (int g = 0; g < a->M_pad; g += vec) {
+      bool pos = false, neg = false;
+      for (int v = 0; v < vec; ++v) {
+        const float x = a->xi_host[g + v];
+        pos = pos || x > 0.f;
+        neg = neg || x < 0.f;
+      }
+      if (pos && neg) {
+        set_error("ordinates %d..%d mix signs of xi; with vec = %d every group of vec consecutive ordinates "
+                  "must share one", g, g + vec - 1, vec);
+        return RT_EINVAL;
+      }
+    }
+  }
 
   // work split (strips of 16 cells, rows per segment as rt_create would choose)
   const int run = 2, tx = cart_tile_width(run);
@@ -241,7 +263,7 @@ extern "C" rt_status rt_cart_stage_noalloc(const rt_cart_stage_args* a) {
   D.n_items = (int32_t)n_items;
   D.n_regions = a->n_regions;
   D.n_cells = (int64_t)a->nx * a->ny;
-  D.n_steps = 1;
+  D.n_steps = a->step + 1;   // the kernel skips instances whose step counter reached n_steps
   D.wait_limit = 4000000000LL;
   D.drop_load = -1;
   D.inv_dx = (float)(1.0 / a->dx);
@@ -265,7 +287,7 @@ extern "C" rt_status rt_cart_stage_noalloc(const rt_cart_stage_args* a) {
   cudaStream_t stream = (cudaStream_t)a->stream;
   cudaError_t e = prepare_cart_stage(kstage, a->order, a->storage, run, vec, ly);
   if (e == cudaSuccess) {
-    noalloc_setup_kernel<<<1, 256, 0, stream>>>(D, n_strips, (int)n_items);
+    noalloc_setup_kernel<<<1, 256, 0, stream>>>(D, n_strips, (int)n_items, a->step);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)

@@ -104,7 +104,8 @@ class rt_cart_stage_args(C.Structure):
                 ("psi_in", C.c_void_p), ("psi_n", C.c_void_p), ("psi_out", C.c_void_p),
                 ("phi_in", C.c_void_p), ("phi_out", C.c_void_p), ("cell_mat", C.c_void_p),
                 ("cell_region", C.c_void_p), ("xi", C.c_void_p), ("eta", C.c_void_p), ("w", C.c_void_p),
-                ("qoi_out", C.c_void_p), ("status_out", C.c_void_p), ("stream", C.c_void_p)]
+                ("qoi_out", C.c_void_p), ("status_out", C.c_void_p), ("stream", C.c_void_p),
+                ("step", C.c_int64), ("xi_host", C.POINTER(C.c_float))]
 
 
 # exported functions: name -> (restype, argtypes)
