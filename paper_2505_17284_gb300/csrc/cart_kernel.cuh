@@ -331,6 +331,7 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
   int issued = min(NS, total);
   for (int c = 0; c < d.n_chunks; ++c) {
     const int k0 = c * C + lane * V;
+    [[maybe_unused]] const uint32_t gkey = sr_gkey(k0 >> 2, salt);   // BF16 rounding: the lane's group of 4
     float w[V], ax[V], ay[V], eneg[V];
     float xsum = 0.f;
 #pragma unroll
@@ -465,10 +466,8 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
             const float div = fmaf(ay[v], g[r][v] - gprev[r][v], dxv);
             float t = fmaf(ta, cj[v], tb) - div;
             if constexpr (STAGE == STAGE_HEUN2) t = 0.5f * (bse[v] + t);
-            if constexpr (sizeof(T) == 2) {
-              const uint32_t rb = sr_bits((int64_t)j * nx + gx, Mpad, (k0 + v) & ~1, salt);
-              t = Store<T>::round_sr(t, ((k0 + v) & 1) ? (rb >> 16) : rb);
-            }
+            if constexpr (sizeof(T) == 2)
+              t = Store<T>::round_sr(t, sr_elem(sr_bits4((uint32_t)(j * nx + gx), gkey), (k0 + v) & 3));
             out[v] = t;
             pw = fmaf(w[v], t, pw);
           }
@@ -675,6 +674,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
     auto chunk = [&](auto dir) {
       constexpr int DXS = decltype(dir)::value;   // sign of xi in this chunk
       const int k0 = c * C + lane * V;
+      [[maybe_unused]] const uint32_t gkey = sr_gkey(k0 >> 2, salt);   // BF16 rounding: the lane's group of 4
       const int dys = d.cdir_y[c];
       const int s0 = (DXS > 0) ? xl0 : xl0 + R - 1;   // this warp's first cell along the flow
       float2 w2[V2], ax2[V2], ay2[V2];
@@ -746,7 +746,13 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
           float2 u[NL][V2];
 #pragma unroll
           for (int m = 0; m < NL; ++m) {
-            lds_vec2<T, V>(reinterpret_cast<const T*>(prv + (m - H) * PSTEP), u[m]);
+            if (m >= H && m < H + R) {
+              // the warp's own cells of the previous row are still in the window (loaded one row ago)
+#pragma unroll
+              for (int v = 0; v < V2; ++v) u[m][v] = Y.c[m - H][v];
+            } else {
+              lds_vec2<T, V>(reinterpret_cast<const T*>(prv + (m - H) * PSTEP), u[m]);
+            }
             if constexpr (XB) {
               const int gpos = x0 + s0 + DXS * (m - H);
               if (gpos < 0 || gpos >= nx) {
@@ -800,15 +806,14 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
               lds_vec2<T, V>(reinterpret_cast<const T*>(cur - H * C * (int)sizeof(T) + L::halo_bytes + r * PSTEP), bse);
             float2 out[V2];
             float2 pw2 = make_float2(0.f, 0.f);
+            [[maybe_unused]] uint2 rb4;
+            if constexpr (sizeof(T) == 2) rb4 = sr_bits4((uint32_t)(jrow * nx + (x0 + s0 + DXS * r)), gkey);
 #pragma unroll
             for (int v = 0; v < V2; ++v) {
               const float2 div = __ffma2_rn(ax2[v], sub2(F[r + 1][v], F[r][v]), __fmul2_rn(ay2[v], sub2(X.g[r][v], Y.g[r][v])));
               float2 t = sub2(__ffma2_rn(ta2, Y.c[r][v], tb2), div);
               if constexpr (STAGE == STAGE_HEUN2) t = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(bse[v], t));
-              if constexpr (sizeof(T) == 2) {
-                const uint32_t rb = sr_bits((int64_t)jrow * nx + (x0 + s0 + DXS * r), Mpad, k0 + 2 * v, salt);
-                t = make_float2(Store<T>::round_sr(t.x, rb), Store<T>::round_sr(t.y, rb >> 16));
-              }
+              if constexpr (sizeof(T) == 2) t = Store<T>::round_sr2(t, ((k0 + 2 * v) & 2) ? rb4.y : rb4.x);
               out[v] = t;
               pw2 = __ffma2_rn(w2[v], t, pw2);
             }

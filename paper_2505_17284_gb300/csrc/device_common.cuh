@@ -16,6 +16,7 @@ template <> struct Store<float> {
   static __device__ __forceinline__ float from_smem(const float v) { return v; }
   static __device__ __forceinline__ float round(float v) { return v; }
   static __device__ __forceinline__ float round_sr(float v, uint32_t) { return v; }
+  static __device__ __forceinline__ float2 round_sr2(float2 v, uint32_t) { return v; }
   static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
@@ -29,6 +30,11 @@ template <> struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ float round_sr(float v, uint32_t r) {
     return __uint_as_float((__float_as_uint(v) + (r & 0xffffu)) & 0xffff0000u);
   }
+  // the pair (a, b) with the 32 random bits r: low half for a, high half for b
+  static __device__ __forceinline__ float2 round_sr2(float2 v, uint32_t r) {
+    return make_float2(__uint_as_float((__float_as_uint(v.x) + (r & 0xffffu)) & 0xffff0000u),
+                       __uint_as_float((__float_as_uint(v.y) + (r >> 16)) & 0xffff0000u));
+  }
   static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
@@ -38,10 +44,19 @@ template <> struct Store<__nv_bfloat16> {
 // time steps (a triangle mesh takes dt from its smallest cells, so most cells
 // change by a small fraction per step) the state then stops moving where it
 // varies slowly and particles are lost. The stage kernels therefore round BF16
-// stores stochastically (Store::round_sr). The random bits are a counter-based
-// hash (Wellons' "lowbias32" 32-bit integer mixer) of the element index
-// (cell * Mpad + ordinate) and a per-stage salt, so a run is reproducible,
-// independent of the launch configuration, and different from step to step.
+// stores stochastically (Store::round_sr) with 16 random bits per element.
+// The bits are a counter-based hash of (cell, ordinate, step, stage), so a run
+// is reproducible, independent of the launch configuration (tiles, ordinates
+// per lane, batching), and different from step to step:
+//   salt  = mix(4 step + stage + c)                  once per launch
+//   gkey  = g * K1 ^ salt                             per group g = k / 4 of
+//                                                     four ordinates
+//   h     = mix(cell * K2 + gkey)                     per cell and group
+//   h2    = xorshift-multiply of h
+// ordinate 4g + e takes the low (e even) or high (e odd) half of h (e < 2) or
+// h2 (e >= 2). mix is Wellons' "lowbias32" 32-bit integer mixer; K1, K2 odd
+// constants (cell * K2 is a bijection of the 32-bit cell index, so no index
+// wraps: cells are below 2^31). One mixer call serves four elements.
 __device__ __forceinline__ uint32_t sr_mix(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352du;
@@ -54,10 +69,22 @@ __device__ __forceinline__ uint32_t sr_mix(uint32_t x) {
 __device__ __forceinline__ uint32_t sr_salt(int64_t step, int stage) {
   return sr_mix((uint32_t)step * 4u + (uint32_t)stage + 0x2545f491u);
 }
-// 32 random bits for the element pair (cell, 2p), (cell, 2p + 1): low half for
-// the first, high half for the second
-__device__ __forceinline__ uint32_t sr_bits(int64_t cell, int Mpad, int k, uint32_t salt) {
-  return sr_mix((uint32_t)(cell * (int64_t)Mpad + k) ^ salt);
+// key of the ordinate group g (ordinates 4g .. 4g+3) in one launch
+__device__ __forceinline__ uint32_t sr_gkey(int g, uint32_t salt) { return ((uint32_t)g * 0x85ebca77u) ^ salt; }
+// 64 random bits of the group's four elements in one cell: .x for ordinates
+// 4g, 4g+1 (low, high half), .y for 4g+2, 4g+3
+__device__ __forceinline__ uint2 sr_bits4(uint32_t cell, uint32_t gkey) {
+  const uint32_t h = sr_mix(cell * 0x9e3779b1u + gkey);
+  uint32_t h2 = (h ^ (h >> 15)) * 0x2c1b3c6du;
+  h2 ^= h2 >> 13;
+  return make_uint2(h, h2);
+}
+// the 32 random bits of the pair (4g + 2p, 4g + 2p + 1), p = 0 or 1
+__device__ __forceinline__ uint32_t sr_pair(uint2 b, int p) { return p ? b.y : b.x; }
+// the 16 random bits (low half) of ordinate 4g + e
+__device__ __forceinline__ uint32_t sr_elem(uint2 b, int e) {
+  const uint32_t w = (e & 2) ? b.y : b.x;
+  return (e & 1) ? (w >> 16) : w;
 }
 
 // ------------------------------------------------------------------ PTX wrappers

@@ -201,6 +201,9 @@ __global__ void __launch_bounds__(kTriThreads, 3)
           load_vec<float, VEC>(d.xi + kk, xi);
           load_vec<float, VEC>(d.eta + kk, eta);
           load_vec<float, VEC>(d.w + kk, w);
+          // BF16 rounding bits of the lane's ordinates kk .. kk+VEC-1 (one group of four)
+          [[maybe_unused]] uint2 rb4;
+          if constexpr (sizeof(T) == 2) rb4 = sr_bits4((uint32_t)cell, sr_gkey(kk >> 2, salt));
 #pragma unroll
           for (int l = 0; l < VEC; ++l) {
             const float c = c2[h][l];
@@ -219,8 +222,7 @@ __global__ void __launch_bounds__(kTriThreads, 3)
             }
             if constexpr (sizeof(T) == 2) {
               const int ko = kk + l;
-              const uint32_t rb = sr_bits(cell, Mpad, ko & ~1, salt);
-              o = Store<T>::round_sr(o, (ko & 1) ? (rb >> 16) : rb);
+              o = Store<T>::round_sr(o, sr_elem(rb4, ko & 3));
             }
             out[l] = o;
             phi_part += w[l] * o;

@@ -45,10 +45,24 @@ CASES = {
     "enclosure40_o2_heun": ("enclosure", 40, 4, 16, 2, "heun", 64),
 }
 
+# Cases whose FP32 check is conditioned on the scheme's own sensitivity to
+# rounding. The second-order scheme on triangles (Green-Gauss gradient,
+# Venkatakrishnan limiter with epsilon = A^3, Sec. 4.2) amplifies rounding-level
+# differences where a discontinuity persists in void: the edges of the inflow
+# beam entering through the opening of the left wall. There the limiter's
+# choices flip on changes of relative size 1e-7, and the FP64 oracle itself,
+# with its state rounded to FP32 after every step, ends 4.9e-3 (relative L2)
+# away from the unrounded oracle at T, 99 % of it in the void next to the
+# opening. No FP32 implementation can stay within 1e-5 of the FP64 trajectory
+# there; the GPU is held to 1e-5 plus three times the distance between the two
+# oracle trajectories (psi, and every QoI), checkpoint by checkpoint.
+ROUNDING_CONDITIONED = ("enclosure40_o2_heun",)
+COND_FACTOR = 3.0
+
 # BF16 storage: bounds at every checkpoint (relative L2 of psi, largest QoI
 # error relative to the QoI or 1e-3 of the mass)
-BF16_PSI = {"lattice140_muscl_heun": 3e-2, "enclosure65_o1_euler": 3e-2, "enclosure40_o2_heun": 3e-2}
-BF16_QOI = {"lattice140_muscl_heun": 1e-2, "enclosure65_o1_euler": 1e-2, "enclosure40_o2_heun": 1e-2}
+BF16_PSI = {"lattice140_muscl_heun": 1.2e-2, "enclosure65_o1_euler": 8e-3, "enclosure40_o2_heun": 2.5e-2}
+BF16_QOI = {"lattice140_muscl_heun": 1.2e-2, "enclosure65_o1_euler": 1.2e-3, "enclosure40_o2_heun": 6e-3}
 
 
 def build_case(name):
@@ -73,9 +87,12 @@ def checkpoints(name, n_t):
     return sorted(set(list(range(every, n_t, every)) + [n_t]))
 
 
-def oracle_job(name):
+def oracle_job(name, round_f32=False):
     """Run the oracle of one case to N_t (in a worker process); returns the
-    state, the time integrals and the integrands at every checkpoint."""
+    state, the time integrals and the integrands at every checkpoint. With
+    round_f32 the state is rounded to FP32 after every step (the oracle's own
+    arithmetic stays FP64): a second trajectory that differs from the first
+    by rounding alone, which measures how the scheme amplifies rounding."""
     p, op, n_t, dt = build_case(name)
     integ = CASES[name][5]
     M = op.M
@@ -84,7 +101,13 @@ def oracle_job(name):
     done = 0
     out = {"n_t": n_t, "dt": dt, "steps": [], "psi": [], "acc": [], "S": []}
     for c in checkpoints(name, n_t):
-        psi, acc, S = oracle.run(op, psi, dt, c - done, integ, acc=acc)
+        if round_f32:
+            for _ in range(c - done):
+                psi, acc, S = oracle.run(op, psi, dt, 1, integ, acc=acc)
+                psi = psi.astype(np.float32).astype(np.float64)
+            S = op.integrands(psi)
+        else:
+            psi, acc, S = oracle.run(op, psi, dt, c - done, integ, acc=acc)
         done = c
         out["steps"].append(c)
         out["psi"].append(psi.copy())
@@ -109,9 +132,11 @@ def start_early():
     for k in saved:
         os.environ[k] = "1"
     try:
-        pool = mp.get_context("spawn").Pool(processes=len(CASES))
+        pool = mp.get_context("spawn").Pool(processes=len(CASES) + len(ROUNDING_CONDITIONED))
         _POOL["pool"] = pool
         _POOL["res"] = {name: pool.apply_async(oracle_job, (name,)) for name in CASES}
+        for name in ROUNDING_CONDITIONED:
+            _POOL["res"][name + ":f32"] = pool.apply_async(oracle_job, (name, True))
     finally:
         for k, v in saved.items():
             if v is None:
@@ -182,8 +207,11 @@ def run_to_final_time(rt, name, storage, ref):
         q = s.qoi()
         assert q["step"] == c
         curve.append({"step": c, "psi_rel_l2": rel_l2(s.psi(), rpsi), "qoi_max_rel": qoi_errors(q, acc, S),
+                      # particle balance relative to the largest of its terms (the enclosure's inflow
+                      # is mostly absorbed by the walls: the flows exceed the mass present by far)
                       "balance": (q["mass"] + sum(q["abs_int"]) + q["outflow_int"] - q["source_int"])
-                      / max(q["source_int"], q["mass"], 1e-300)})
+                      / max(abs(q["mass"]), sum(abs(v) for v in q["abs_int"]), abs(q["outflow_int"]),
+                            abs(q["source_int"]), 1e-300)})
     s.close()
     log = os.environ.get("RT_ERROR_LOG")
     if log:
@@ -193,14 +221,37 @@ def run_to_final_time(rt, name, storage, ref):
     return curve
 
 
+def rounding_spread(ref, rnd):
+    """Per checkpoint: distance of the FP32-rounded oracle trajectory from the
+    unrounded one (relative L2 of psi, largest QoI error)."""
+    out = []
+    for k in range(len(ref["steps"])):
+        q = {"mass": rnd["S"][k]["mass"], "outflow_now": rnd["S"][k]["outflow"],
+             "outflow_int": rnd["acc"][k]["outflow_int"], "abs_now": rnd["S"][k]["abs"],
+             "abs_int": rnd["acc"][k]["abs_int"], "box_out_now": rnd["S"][k].get("box_out", ()),
+             "box_out_int": rnd["acc"][k]["box_out_int"]}
+        out.append((rel_l2(rnd["psi"][k], ref["psi"][k]), qoi_errors(q, ref["acc"][k], ref["S"][k])))
+    return out
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp32_matches_the_oracle_up_to_T(rt, oracle_runs, name):
     ref = oracle_runs[name].get(timeout=1800)
     curve = run_to_final_time(rt, name, rt.RT_FP32, ref)
-    for pt in curve:
-        assert pt["psi_rel_l2"] <= PSI_TOL, pt
-        assert pt["qoi_max_rel"] <= QOI_TOL, pt
+    if name in ROUNDING_CONDITIONED:
+        spread = rounding_spread(ref, oracle_runs[name + ":f32"].get(timeout=1800))
+    else:
+        spread = [(0.0, 0.0)] * len(curve)
+    for pt, (sp, sq) in zip(curve, spread):
+        assert pt["psi_rel_l2"] <= PSI_TOL + COND_FACTOR * sp, (pt, sp)
+        assert pt["qoi_max_rel"] <= QOI_TOL + COND_FACTOR * sq, (pt, sq)
         assert abs(pt["balance"]) <= 1e-5, pt
+    log = os.environ.get("RT_ERROR_LOG")
+    if log and name in ROUNDING_CONDITIONED:
+        with open(log, "a") as fh:
+            fh.write(json.dumps({"case": name, "storage": "oracle_f32_rounded",
+                                 "curve": [{"step": c, "psi_rel_l2": a, "qoi_max_rel": b}
+                                           for c, (a, b) in zip(ref["steps"], spread)]}) + "\n")
 
 
 @pytest.mark.parametrize("name", list(CASES))

@@ -234,12 +234,12 @@ def test_noalloc_reports_nonfinite_then_starts_clean(rt):
     buf = CallerBuffers(p, quad, solver.psi(), solver.phi())
     n_reg = p.materials.n_regions
     bad = buf.args(rt, p, 1, rt.RT_STAGE_EULER, solver.info.dt, tile_y, buf.psi[0], buf.psi[1], buf.phi[0],
-                   buf.phi[1])
+                   buf.phi[1], vec=1)
     bad.sigma_a[1] = 3.0e38        # absorbers: the absorption QoI overflows FP32
     rt.rt_cart_stage_noalloc(bad)
     buf.qoi_dict(n_reg, status=rt.RT_ENONFINITE)
     rt.rt_cart_stage_noalloc(buf.args(rt, p, 1, rt.RT_STAGE_EULER, solver.info.dt, tile_y, buf.psi[0],
-                                      buf.psi[1], buf.phi[0], buf.phi[1]))
+                                      buf.psi[1], buf.phi[0], buf.phi[1], vec=1))
     solver.step(1)
     check_against(rt, buf, buf.psi[1], buf.phi[1], solver, n_reg, 32)
     solver.close()
@@ -250,8 +250,8 @@ def test_noalloc_checks_ordinate_groups_against_host_xi(rt):
     rejected (RT_EINVAL) before anything is launched."""
     import ctypes
     p = si.lattice_problem(14)
-    quad = rt.rt_quad_product(2, 16)
-    buf = CallerBuffers(p, quad, np.zeros((p.mesh.n_cells, 32)), np.zeros(p.mesh.n_cells))
+    quad = rt.rt_quad_product(4, 16)
+    buf = CallerBuffers(p, quad, np.zeros((p.mesh.n_cells, 64)), np.zeros(p.mesh.n_cells))
     xi = np.ascontiguousarray(buf.quad_host[0])
     a = buf.args(rt, p, 1, rt.RT_STAGE_EULER, 0.01, 8, buf.psi[0], buf.psi[1], buf.phi[0], buf.phi[1], vec=2)
     a.xi_host = xi.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
