@@ -115,8 +115,12 @@ typedef struct {
 
 /* Boundary per side (x-, x+, y-, y+): RT_BC_VACUUM (psi^- = 0), RT_BC_INFLOW
  * (isotropic psi^- = inflow[side] for ordinates entering through that side) or
- * RT_BC_PERIODIC (accepted by rt_create only on the CPU oracle side; the GPU
- * path rejects it with RT_EINVAL). */
+ * RT_BC_PERIODIC. Periodic sides come in pairs (x- with x+, y- with y+) and
+ * are supported on Cartesian meshes: the cell across a periodic side is the
+ * cell at the other end of the row or column, so the axis has no boundary
+ * faces (its fluxes telescope, Sec. 4.2, and nothing leaves through it; MUSCL
+ * slopes and faces stay second order there). RT_EINVAL for an unpaired
+ * periodic side or a periodic side of a triangle mesh. */
 typedef struct {
   int32_t side_kind[4];
   double inflow[4];
@@ -383,6 +387,15 @@ rt_status rt_batch_step(rt_batch* b, int64_t n);
 /* Advance every problem to its own N_t (at most max_steps steps per problem
  * when max_steps > 0); enqueues and returns. */
 rt_status rt_batch_run(rt_batch* b, int64_t max_steps);
+
+/* Hold (hold != 0) or release (hold = 0) the problem in `slot`: a held problem
+ * keeps its state on the device but is left out of rt_batch_step and
+ * rt_batch_run until released, so a scheduler can choose which problems the
+ * shared launches advance (the serving loop gives the GPU to the oldest
+ * requests first). The paper has no counterpart. Takes effect at the next
+ * step (the work list is rebuilt then); no synchronisation. RT_EINVAL for an
+ * empty slot. */
+rt_status rt_batch_hold(rt_batch* b, int32_t slot, int32_t hold);
 
 /* Steps enqueued so far for the problem in `slot` and its N_t (no
  * synchronisation). RT_EINVAL for an empty slot. */

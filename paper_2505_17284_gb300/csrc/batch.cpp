@@ -31,6 +31,7 @@ struct Group {
 
 struct Slot {
   bool used = false;
+  bool held = false;   // left out of the work list until released (rt_batch_hold)
   std::unique_ptr<DeviceArena> arena;
   Instance inst;
   WorkItem* d_init_items = nullptr;
@@ -147,7 +148,7 @@ rt_status rebuild(rt_batch* b) {
   b->members.clear();
   for (int i = 0; i < (int)b->slots.size(); ++i) {
     const Slot& S = b->slots[i];
-    if (!S.used || S.done >= S.inst.n_steps) continue;
+    if (!S.used || S.held || S.done >= S.inst.n_steps) continue;
     const Instance& I = S.inst;
     by_variant[std::make_tuple(I.kind, I.order, I.integrator, I.run, I.cvec, I.vec, I.uni)].push_back(i);
     b->members.push_back(i);
@@ -369,8 +370,21 @@ rt_status rt_batch_remove(rt_batch* b, int32_t i) {
   S.arena->free_all();
   S.arena.reset();
   S.used = false;
+  S.held = false;
   S.done = 0;
   b->dirty = true;
+  return RT_OK;
+}
+
+rt_status rt_batch_hold(rt_batch* b, int32_t i, int32_t hold) {
+  clear_error();
+  if (!b) { set_error("batch is NULL"); return RT_EINVAL; }
+  if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
+  const bool h = hold != 0;
+  if (b->slots[i].held != h) {
+    b->slots[i].held = h;
+    b->dirty = true;   // the work list (and its graph) changes at the next step
+  }
   return RT_OK;
 }
 
@@ -393,7 +407,7 @@ rt_status rt_batch_run(rt_batch* b, int64_t max_steps) {
     // steps until the next problem finishes
     int64_t phase = INT64_MAX;
     for (const Slot& S : b->slots)
-      if (S.used && S.done < S.inst.n_steps) phase = std::min(phase, S.inst.n_steps - S.done);
+      if (S.used && !S.held && S.done < S.inst.n_steps) phase = std::min(phase, S.inst.n_steps - S.done);
     if (phase == INT64_MAX) break;
     phase = std::min(phase, budget);
     int64_t left = phase;

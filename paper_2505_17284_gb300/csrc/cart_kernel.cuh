@@ -71,6 +71,10 @@ size_t cart_smem_for(int ly) {
   return L::ring_bytes + cart_tile_bytes(L::TX, ly) + kCartFixedBytes;
 }
 
+// Index of cell or row g on a periodic axis of n cells (g may lie a few cells
+// outside 0..n-1).
+__device__ __forceinline__ int wrap_index(int g, int n) { return ((g % n) + n) % n; }
+
 // minmod(a, b) = median(a, b, 0): 0 unless a and b share a sign, else the one of
 // smaller magnitude.
 __device__ __forceinline__ float minmod_med(float a, float b) {
@@ -277,7 +281,10 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
     const int c = q / Lc;
     const int p = ya - H + (q - c * Lc);
     uint8_t* dst = ring + slot * L::slot_bytes;
-    const bool halo = (p >= 0 && p < ny);
+    // rows outside the domain: the wrapped row on a periodic axis, else none (ghost values)
+    const bool wrapped = (p < 0 || p >= ny) && d.periodic_y;   // interior rows read no flag
+    const bool halo = (p >= 0 && p < ny) || wrapped;
+    const int pl = wrapped ? wrap_index(p, ny) : p;
     const bool base = (STAGE == STAGE_HEUN2) && (p - H >= ya);
     const uint32_t bytes = (halo ? L::halo_bytes : 0) + (base ? L::base_bytes : 0);
     if ((int64_t)q == d.drop_load) return;   // test hook: this slot never completes
@@ -286,7 +293,7 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
       return;
     }
     mbar_arrive_expect_tx(&bars[slot], bytes);
-    if (halo) tma_load_3d(dst, map_halo, &bars[slot], c * C, x0 - H, p);
+    if (halo) tma_load_3d(dst, map_halo, &bars[slot], c * C, x0 - H, pl);
     if (base) tma_load_3d(dst + L::halo_bytes, map_base, &bars[slot], c * C, x0, p - H);
   };
 
@@ -360,7 +367,7 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
       const T* srow = reinterpret_cast<const T*>(ring + slot * L::slot_bytes);
       // ---- the new row p: own cells, in upwind order
       float c0[R][V];
-      if (YB && (p < 0 || p >= ny)) {
+      if (YB && !d.periodic_y && (p < 0 || p >= ny)) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const float etav = d.eta[k0 + v];
@@ -388,7 +395,7 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
       float g[R][V];
       if constexpr (ORDER == 2) {
         float hmul = 0.5f;
-        if (YB) hmul = (f == -1 || f == ny - 1) ? 0.f : 0.5f;
+        if (YB && !d.periodic_y) hmul = (f == -1 || f == ny - 1) ? 0.f : 0.5f;
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -421,10 +428,16 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
           if constexpr (XB) {
             const int gpos = x0 + pos;
             if (gpos < 0 || gpos >= nx) {
+              if (d.periodic_x) {
+                // periodic: the wrapped cell of the same row, from the input state
+                lds_vec<T, V>(reinterpret_cast<const T*>(d.psi[in_buf]) + ((size_t)j * nx + wrap_index(gpos, nx)) * Mpad + k0,
+                              u[m]);
+              } else {
 #pragma unroll
-              for (int v = 0; v < V; ++v) {
-                const float xiv = d.xi[k0 + v];
-                u[m][v] = (gpos < 0) ? ((xiv > 0.f) ? d.ghost[0] : 0.f) : ((xiv < 0.f) ? d.ghost[1] : 0.f);
+                for (int v = 0; v < V; ++v) {
+                  const float xiv = d.xi[k0 + v];
+                  u[m][v] = (gpos < 0) ? ((xiv > 0.f) ? d.ghost[0] : 0.f) : ((xiv < 0.f) ? d.ghost[1] : 0.f);
+                }
               }
             }
           }
@@ -436,7 +449,7 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
           float h = (ORDER == 2) ? 0.5f : 0.f;
           if constexpr (XB) {
             const int ga = x0 + s0 + dxs * m, gb = ga + dxs;
-            if (!((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) h = 0.f;
+            if (!d.periodic_x && !((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) h = 0.f;
           }
 #pragma unroll
           for (int v = 0; v < V; ++v) {
@@ -480,10 +493,10 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 const float o = out[v], xiv = d.xi[k0 + v], etav = d.eta[k0 + v];
-                if (XB && gx == 0) bacc += ly_f * (w[v] * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
-                if (XB && gx == nx - 1) bacc += ly_f * (w[v] * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
-                if (YB && j == 0) bacc += lx_f * (w[v] * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
-                if (YB && j == ny - 1) bacc += lx_f * (w[v] * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
+                if (XB && !d.periodic_x && gx == 0) bacc += ly_f * (w[v] * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
+                if (XB && !d.periodic_x && gx == nx - 1) bacc += ly_f * (w[v] * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
+                if (YB && !d.periodic_y && j == 0) bacc += lx_f * (w[v] * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
+                if (YB && !d.periodic_y && j == ny - 1) bacc += lx_f * (w[v] * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
               }
             }
           }
@@ -530,8 +543,11 @@ __device__ __forceinline__ void cart_tile(const InstDesc& d, const WorkItem& it,
 }
 
 // One row pull of the chunk-uniform tile: pull e (chunk c, row i of the chunk)
-// into ring slot `slot`, completing full[slot].
-template <typename L>
+// into ring slot `slot`, completing full[slot]. Only tiles that touch the y
+// sides of the domain (YB) pull rows outside it: the wrapped row on a periodic
+// axis, else nothing (the ghost values are set in registers); interior tiles
+// skip those tests, since the issuing thread is on the ring's critical path.
+template <typename L, bool YB>
 struct UniPull {
   const InstDesc* d;
   uint8_t* ring;
@@ -546,7 +562,14 @@ struct UniPull {
     const int dy = d->cdir_y[c];
     const int p = ((dy > 0) ? ya : yb - 1) + dy * (i - H);
     uint8_t* dst = ring + slot * L::slot_bytes;
-    const bool halo = (p >= 0 && p < d->ny);
+    bool halo = true;
+    int pl = p;
+    if constexpr (YB) {
+      if (p < 0 || p >= d->ny) {
+        halo = d->periodic_y != 0;
+        if (halo) pl = wrap_index(p, d->ny);
+      }
+    }
     const bool base = L::base_bytes > 0 && (i >= H + 1);   // Heun stage 2: psi^n of the row completed here
     const uint32_t bytes = (halo ? L::halo_bytes : 0) + (base ? L::base_bytes : 0);
     slot_pull[slot] = e;
@@ -556,7 +579,7 @@ struct UniPull {
       return;
     }
     mbar_arrive_expect_tx(&full[slot], bytes);
-    if (halo) tma_load_3d(dst, map_halo, &full[slot], c * C, x0 - H, p);
+    if (halo) tma_load_3d(dst, map_halo, &full[slot], c * C, x0 - H, pl);
     if (base) tma_load_3d(dst + L::halo_bytes, map_base, &full[slot], c * C, x0, p - dy);
   }
 };
@@ -620,7 +643,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   double* red = reinterpret_cast<double*>(smem + L::ring_bytes + 128 + cart_tile_bytes(TX, d.ly));
   const int64_t limit = d.wait_limit;
   static_assert(NS * (8 + 4) <= 128, "ring control block must fit its 128 bytes");
-  const UniPull<L> pull{&d, ring, full, slot_pull, map_halo, map_base, x0, ya, yb};
+  const UniPull<L, YB> pull{&d, ring, full, slot_pull, map_halo, map_base, x0, ya, yb};
 
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -707,7 +730,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
         const bool wok = mbar_wait_bounded(&full[slot], ph, limit);
         const uint8_t* cur = ring + slot * L::slot_bytes + lofs;
         bool p_in = true;
-        if constexpr (YB) p_in = (p >= 0 && p < ny);
+        if constexpr (YB) p_in = d.periodic_y || (p >= 0 && p < ny);
         if (YB && !p_in) {
           const float gv = (i < H) ? gy_up : 0.f;   // after the tile only the first-order face sees it
 #pragma unroll
@@ -723,7 +746,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
           bool second = true;
           if constexpr (YB) {
             const int pp = p - dys;
-            if ((pp >= 0 && pp < ny) != p_in) second = false;   // domain boundary face: first order
+            if (!d.periodic_y && (pp >= 0 && pp < ny) != p_in) second = false;   // domain boundary face: first order
           }
 #pragma unroll
           for (int r = 0; r < R; ++r)
@@ -756,12 +779,18 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
             if constexpr (XB) {
               const int gpos = x0 + s0 + DXS * (m - H);
               if (gpos < 0 || gpos >= nx) {
-                // entering ordinates see psi^- of the side, leaving ones nothing (only
-                // first-order faces read it)
-                const float gside = (gpos < 0) ? d.ghost[0] : d.ghost[1];
-                const bool enter = (gpos < 0) == (DXS > 0);
+                if (d.periodic_x) {
+                  // periodic: the wrapped cell of the same row, from the input state
+                  lds_vec2<T, V>(reinterpret_cast<const T*>(d.psi[in_buf]) + ((size_t)jrow * nx + wrap_index(gpos, nx)) * Mpad + k0,
+                                 u[m]);
+                } else {
+                  // entering ordinates see psi^- of the side, leaving ones nothing (only
+                  // first-order faces read it)
+                  const float gside = (gpos < 0) ? d.ghost[0] : d.ghost[1];
+                  const bool enter = (gpos < 0) == (DXS > 0);
 #pragma unroll
-                for (int v = 0; v < V2; ++v) u[m][v] = enter ? make_float2(gside, gside) : make_float2(0.f, 0.f);
+                  for (int v = 0; v < V2; ++v) u[m][v] = enter ? make_float2(gside, gside) : make_float2(0.f, 0.f);
+                }
               }
             }
           }
@@ -781,7 +810,7 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
               bool second = true;
               if constexpr (XB) {
                 const int ga = x0 + s0 + DXS * m, gb = ga + DXS;
-                if (!((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) second = false;
+                if (!d.periodic_x && !((ga >= 0 && ga < nx) && (gb >= 0 && gb < nx))) second = false;
               }
 #pragma unroll
               for (int v = 0; v < V2; ++v)
@@ -828,10 +857,10 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
                   const float o = (v & 1) ? out[v / 2].y : out[v / 2].x;
                   const float wv = (v & 1) ? w2[v / 2].y : w2[v / 2].x;
                   const float xiv = d.xi[k0 + v], etav = d.eta[k0 + v];
-                  if (XB && gx == 0) bacc += ly_f * (wv * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
-                  if (XB && gx == nx - 1) bacc += ly_f * (wv * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
-                  if (YB && jrow == 0) bacc += lx_f * (wv * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
-                  if (YB && jrow == ny - 1) bacc += lx_f * (wv * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
+                  if (XB && !d.periodic_x && gx == 0) bacc += ly_f * (wv * -xiv * (xiv < 0.f ? o : (xiv > 0.f ? d.ghost[0] : 0.f)));
+                  if (XB && !d.periodic_x && gx == nx - 1) bacc += ly_f * (wv * xiv * (xiv > 0.f ? o : (xiv < 0.f ? d.ghost[1] : 0.f)));
+                  if (YB && !d.periodic_y && jrow == 0) bacc += lx_f * (wv * -etav * (etav < 0.f ? o : (etav > 0.f ? d.ghost[2] : 0.f)));
+                  if (YB && !d.periodic_y && jrow == ny - 1) bacc += lx_f * (wv * etav * (etav > 0.f ? o : (etav < 0.f ? d.ghost[3] : 0.f)));
                 }
               }
             }
@@ -889,6 +918,11 @@ __device__ __forceinline__ void cart_tile_uni(const InstDesc& d, const WorkItem&
   cart_epilogue<TX, STAGE>(d, it, phi_out, tile_acc, red, x0, ya, nrows, bacc);
 }
 
+template <int ORDER, int R, int V, int STAGE, typename T, bool XB, bool YB>
+__device__ __noinline__ void cart_tile_uni_edge(const InstDesc* dp, const WorkItem it, InstState* st, uint8_t* smem) {
+  cart_tile_uni<ORDER, R, V, STAGE, T, XB, YB>(*dp, it, st, smem);
+}
+
 template <int ORDER, int R, int V, int STAGE, typename T, bool UNI>
 __global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
     cart_stage_kernel(const InstDesc* __restrict__ descs, const WorkItem* __restrict__ items) {
@@ -906,11 +940,14 @@ __global__ void __launch_bounds__(kCartThreads, (R * V >= 8 ? 2 : 3))
   const bool xb = (x0 - L::H < 0) || (x0 + L::TX + L::H > d.nx);
   const bool yb = (ya - L::H < 0) || (ya + d.ly + L::H > d.ny);
   if constexpr (UNI) {
+    // tiles on the domain boundary run out of line, so that their extra state
+    // (ghost values, wrapped rows and cells) does not raise the register
+    // pressure of the interior tiles
     if (xb) {
-      if (yb) cart_tile_uni<ORDER, R, V, STAGE, T, true, true>(d, it, st, smem);
-      else cart_tile_uni<ORDER, R, V, STAGE, T, true, false>(d, it, st, smem);
+      if (yb) cart_tile_uni_edge<ORDER, R, V, STAGE, T, true, true>(&d, it, st, smem);
+      else cart_tile_uni_edge<ORDER, R, V, STAGE, T, true, false>(&d, it, st, smem);
     } else {
-      if (yb) cart_tile_uni<ORDER, R, V, STAGE, T, false, true>(d, it, st, smem);
+      if (yb) cart_tile_uni_edge<ORDER, R, V, STAGE, T, false, true>(&d, it, st, smem);
       else cart_tile_uni<ORDER, R, V, STAGE, T, false, false>(d, it, st, smem);
     }
   } else {

@@ -146,10 +146,13 @@ static rt_status validate_common(const rt_materials* mat, const rt_quadrature* q
   }
   for (int s = 0; s < 4; ++s) {
     const int k = bc->side_kind[s];
-    if (k == RT_BC_PERIODIC) { set_error("periodic sides are not supported by the GPU path"); return RT_EINVAL; }
-    if (k != RT_BC_VACUUM && k != RT_BC_INFLOW) { set_error("side %d: unknown boundary kind %d", s, k); return RT_EINVAL; }
+    if (k != RT_BC_VACUUM && k != RT_BC_INFLOW && k != RT_BC_PERIODIC) { set_error("side %d: unknown boundary kind %d", s, k); return RT_EINVAL; }
     if (k == RT_BC_INFLOW && !std::isfinite(bc->inflow[s])) { set_error("side %d: inflow must be finite", s); return RT_EINVAL; }
   }
+  for (int a = 0; a < 2; ++a)
+    if ((bc->side_kind[2 * a] == RT_BC_PERIODIC) != (bc->side_kind[2 * a + 1] == RT_BC_PERIODIC)) {
+      set_error("periodic sides come in pairs (x-/x+ or y-/y+)"); return RT_EINVAL;
+    }
   return RT_OK;
 }
 
@@ -537,6 +540,11 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   }
   rt_status s = validate_common(mat, quad, bc, order, integrator, storage, t_end, n_cells);
   if (s != RT_OK) return s;
+  if (mesh->kind == RT_MESH_TRIANGLES)
+    for (int sd = 0; sd < 4; ++sd)
+      if (bc->side_kind[sd] == RT_BC_PERIODIC) {
+        set_error("periodic sides are supported on Cartesian meshes only"); return RT_EINVAL;
+      }
   std::vector<int4> box_faces;
   if ((s = build_box_faces(mesh, mat, box_faces)) != RT_OK) return s;
   if (std::isnan(dt_target)) { set_error("dt is not a number"); return RT_EINVAL; }
@@ -829,6 +837,8 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   }
   D.dt = (float)I.dt; D.dt_d = I.dt;
   for (int sd = 0; sd < 4; ++sd) D.ghost[sd] = bc->side_kind[sd] == RT_BC_INFLOW ? (float)bc->inflow[sd] : 0.f;
+  D.periodic_x = bc->side_kind[0] == RT_BC_PERIODIC ? 1 : 0;
+  D.periodic_y = bc->side_kind[2] == RT_BC_PERIODIC ? 1 : 0;
   D.uni = I.uni;
   for (int c = 0; c < kMaxUniChunks; ++c) {
     D.cdir_x[c] = cdx[c];

@@ -102,6 +102,8 @@ struct alignas(128) InstDesc {
   // FP32 [cell][2][Mpad] (x row, then y row)
   const float4* tri_geo2;
   float* tri_lg;
+  int32_t periodic_x;           // Cartesian: 1 if the x- and x+ sides are periodic (no boundary faces in x)
+  int32_t periodic_y;           // Cartesian: 1 if the y- and y+ sides are periodic
 };
 
 struct WorkItem {

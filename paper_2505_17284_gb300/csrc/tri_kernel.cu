@@ -352,10 +352,11 @@ __global__ void __launch_bounds__(kTriThreads)
       m = d.mat[cell];
       reg = d.region[cell];
       const float ly = (float)d.dy_d, lx = (float)d.dx_d;
-      if (i == 0) { fx[nf] = -ly; fy[nf] = 0.f; gh[nf] = d.ghost[0]; ++nf; }
-      if (i == d.nx - 1) { fx[nf] = ly; fy[nf] = 0.f; gh[nf] = d.ghost[1]; ++nf; }
-      if (j == 0) { fx[nf] = 0.f; fy[nf] = -lx; gh[nf] = d.ghost[2]; ++nf; }
-      if (j == d.ny - 1) { fx[nf] = 0.f; fy[nf] = lx; gh[nf] = d.ghost[3]; ++nf; }
+      // boundary faces (a periodic axis has none)
+      if (!d.periodic_x && i == 0) { fx[nf] = -ly; fy[nf] = 0.f; gh[nf] = d.ghost[0]; ++nf; }
+      if (!d.periodic_x && i == d.nx - 1) { fx[nf] = ly; fy[nf] = 0.f; gh[nf] = d.ghost[1]; ++nf; }
+      if (!d.periodic_y && j == 0) { fx[nf] = 0.f; fy[nf] = -lx; gh[nf] = d.ghost[2]; ++nf; }
+      if (!d.periodic_y && j == d.ny - 1) { fx[nf] = 0.f; fy[nf] = lx; gh[nf] = d.ghost[3]; ++nf; }
     }
     float ph_part = 0.f, bpart = 0.f;
     for (int v = 0; v < nv; ++v) {

@@ -132,6 +132,7 @@ SIGNATURES = {
                                   C.POINTER(C.c_void_p)]),
     "rt_batch_add": (C.c_int, [C.c_void_p, C.POINTER(rt_problem), C.POINTER(C.c_int32)]),
     "rt_batch_remove": (C.c_int, [C.c_void_p, C.c_int32]),
+    "rt_batch_hold": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "rt_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "rt_batch_progress": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "rt_batch_run": (C.c_int, [C.c_void_p, C.c_int64]),
@@ -501,6 +502,9 @@ class Batch:
     def remove(self, slot: int):
         check(_fns().rt_batch_remove(self.h, slot))
         self.shapes.pop(slot, None)
+
+    def hold(self, slot: int, hold: bool = True):
+        check(_fns().rt_batch_hold(self.h, slot, 1 if hold else 0))
 
     def step(self, n: int):
         check(_fns().rt_batch_step(self.h, int(n)))

@@ -3,15 +3,24 @@
 Solve requests arrive over time. The server keeps one batch of slots on the
 GPU: an arrived request is admitted (its problem built, its state created and
 initialised on the device) as soon as a slot is free and its device memory
-fits in a budget taken from the free HBM at start; every admitted problem is
-advanced together with the others, in chunks of steps, by the same launches;
-a problem that reaches its own N_t is retired (QoIs read back, memory freed)
+fits both the server's budget and the device memory free at that moment; a
+problem that reaches its own N_t is retired (QoIs read back, memory freed)
 and its slot and memory go to the next request. State stays on the device
 from admission to retirement. Latency is retirement time minus arrival time.
 
-The plain baseline serves the same stream first-in first-out with one solver
-at a time; its latencies follow from the measured service time of each
-request (a single FIFO server's latency does not depend on anything else).
+Which admitted problems the shared launches advance is the scheduler's
+choice (policy "fcfs_fill", the default): the oldest request always runs,
+and younger ones join it, oldest first, while the per-step state traffic of
+the chosen set stays within `fill_bytes` (the traffic that keeps the GPU
+busy); the others are held on the device (rt_batch_hold) until capacity frees
+up. Large requests thus run at nearly the speed they would have alone, in
+arrival order, while small requests fill the capacity that one large request
+leaves idle. Policy "all" advances every admitted problem together (processor
+sharing, which stretches large requests by the number sharing the GPU).
+
+The plain baseline is a first-in first-out server that solves one request
+at a time with the single-problem entry points, run against the same arrival
+times (serve_fifo).
 """
 from __future__ import annotations
 
@@ -62,15 +71,46 @@ def estimate_bytes(n_cells: int, M: int, storage=rt.RT_FP32, triangles=False, or
     return int(n_cells * per_cell + (8 << 20))
 
 
+def step_bytes(job, storage=rt.RT_FP32) -> float:
+    """Algorithmic state bytes one time step of a job moves (psi reads and
+    writes; Heun 5 values per cell and ordinate, Euler 2)."""
+    es = 2 if storage == rt.RT_BF16 else 4
+    Mpad = (job.M + 31) // 32 * 32
+    return float(job.n_cells) * Mpad * es * (5 if job.integrator == rt.RT_HEUN else 2)
+
+
+def live_free_bytes() -> int:
+    """Device memory available right now: free in the driver plus what
+    PyTorch's caching allocator holds but does not use."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return int(free + torch.cuda.memory_reserved() - torch.cuda.memory_allocated())
+
+
 @dataclass
 class Server:
     storage: int = rt.RT_FP32
     capacity: int = 64             # slots
     chunk: int = 16                # steps per enqueue
-    mem_fraction: float = 0.85     # of the free HBM at start
+    policy: str = "fcfs_fill"      # or "all" (every admitted problem advances)
+    fill_bytes: float = 2.0e9      # per-step state traffic of the advanced set (fcfs_fill)
+    mem_fraction: float = 0.85     # of the device memory free at start: the server's budget
     reserve: int = 2 << 30         # bytes kept free for the allocator's own use
     max_ahead: int = 2             # chunks enqueued ahead of the device
     log: list = field(default_factory=list)
+
+    def select(self, active, weight):
+        """Slots to advance: all (policy "all"), or the oldest first while the
+        summed per-step traffic stays within fill_bytes (the oldest always)."""
+        order = sorted(active, key=lambda s: (active[s][0].arrival, active[s][0].rid))
+        if self.policy == "all":
+            return set(order)
+        chosen, acc = set(), 0.0
+        for s in order:
+            if not chosen or acc + weight[s] <= self.fill_bytes:
+                chosen.add(s)
+                acc += weight[s]
+        return chosen
 
     def run(self, requests, realtime=True):
         """Serve `requests` (arrival times relative to the start); with
@@ -82,6 +122,8 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting = collections.deque()
         active = {}                     # slot -> (request, admitted time, bytes)
+        weight = {}                     # slot -> state bytes per step
+        held = set()
         used = 0
         events = collections.deque()
         done = []
@@ -93,11 +135,13 @@ class Server:
                 t = now()
                 while pending and (not realtime or pending[0].arrival <= t):
                     waiting.append(pending.popleft())
-                while waiting and len(active) < self.capacity and used + waiting[0].est_bytes <= budget:
+                while (waiting and len(active) < self.capacity and used + waiting[0].est_bytes <= budget
+                       and waiting[0].est_bytes + self.reserve <= live_free_bytes()):
                     r = waiting.popleft()
                     j = r.make()
                     slot = b.add(j.problem, j.quad, order=j.order, integrator=j.integrator, dt=j.dt)
                     active[slot] = (r, now(), r.est_bytes)
+                    weight[slot] = step_bytes(j, self.storage)
                     used += r.est_bytes
                 if not active:
                     if waiting:
@@ -106,12 +150,18 @@ class Server:
                     if pending:
                         time.sleep(max(0.0, pending[0].arrival - now()))
                     continue
+                run = self.select(active, weight)
+                for slot in active:
+                    h = slot not in run
+                    if h != (slot in held):
+                        b.hold(slot, h)
+                        (held.add if h else held.discard)(slot)
                 b.step(self.chunk)
                 ev = torch.cuda.Event()
                 ev.record()
                 events.append(ev)
                 finished = []
-                for slot in active:
+                for slot in run:
                     d, n = b.progress(slot)
                     if d >= n:
                         finished.append(slot)
@@ -119,6 +169,8 @@ class Server:
                     for slot in finished:
                         q = b.qoi(slot)          # synchronises
                         r, adm, nb = active.pop(slot)
+                        weight.pop(slot)
+                        held.discard(slot)
                         done.append(Served(r.rid, r.arrival, adm, now(), q, slot))
                         b.remove(slot)
                         used -= nb
@@ -128,6 +180,30 @@ class Server:
         finally:
             b.close()
         return done
+
+
+def serve_fifo(requests, storage=rt.RT_FP32, realtime=True, tune=False):
+    """The plain server: first in, first out, one request at a time through
+    the single-problem entry points (build, create, step to N_t, read the QoIs,
+    destroy), against the requests' arrival times. Returns the list of Served
+    in completion order."""
+    import torch
+    pending = sorted(requests, key=lambda r: r.arrival)
+    done = []
+    t0 = time.perf_counter()
+    now = lambda: time.perf_counter() - t0
+    for r in pending:
+        if realtime and r.arrival > now():
+            time.sleep(r.arrival - now())
+        start = now()
+        j = r.make()
+        s = rt.Solver(j.problem, j.quad, order=j.order, integrator=j.integrator, storage=storage, dt=j.dt, tune=tune)
+        s.step()
+        q = s.qoi()
+        s.close()
+        torch.cuda.synchronize()
+        done.append(Served(r.rid, r.arrival, start, now(), q))
+    return done
 
 
 def plain_service_times(requests, storage=rt.RT_FP32, tune=False):

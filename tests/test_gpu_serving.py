@@ -89,14 +89,16 @@ MIX = [("lattice", 21, 2, 16), ("enclosure", 8, 2, 8), ("lattice", 28, 4, 16), (
        ("lattice", 14, 2, 8), ("lattice", 35, 8, 16), ("enclosure", 6, 2, 16), ("lattice", 21, 4, 16)]
 
 
-@pytest.mark.parametrize("realtime", [False, True])
-def test_served_results_equal_alone(rt, realtime):
+@pytest.mark.parametrize("realtime,policy,fill", [(False, "fcfs_fill", 2e9), (True, "fcfs_fill", 2e9),
+                                                  (True, "all", 0.0), (False, "fcfs_fill", 6e5)])
+def test_served_results_equal_alone(rt, realtime, policy, fill):
     """Three slots for eight requests: later requests wait for slots, join the
-    batch while others are mid-solve, and every result is bit-identical to the
-    request solved alone."""
+    batch while others are mid-solve (or are held while older ones run, with a
+    small fill), and every result is bit-identical to the request solved
+    alone."""
     from paper_2505_17284_gb300 import serve as SV
     reqs = stream(rt, MIX)
-    served = SV.Server(capacity=3, chunk=4).run(reqs, realtime=realtime)
+    served = SV.Server(capacity=3, chunk=4, policy=policy, fill_bytes=fill).run(reqs, realtime=realtime)
     assert sorted(s.rid for s in served) == list(range(len(MIX)))
     assert max(s.admitted - s.arrival for s in served) > 0      # some request waited for a slot
     assert len({s.slot for s in served}) <= 3
@@ -149,3 +151,32 @@ def test_admission_by_memory_budget(rt):
     big[0].est_bytes = int(free) * 2
     with pytest.raises(RuntimeError):
         SV.Server(capacity=2).run(big, realtime=False)
+
+
+def test_fcfs_fill_runs_the_oldest_first(rt):
+    """With a fill smaller than any request, the scheduler advances only the
+    oldest admitted request: requests finish in arrival order although later
+    ones were admitted (held on the device) long before."""
+    from paper_2505_17284_gb300 import serve as SV
+    reqs = stream(rt, MIX[:5])
+    served = SV.Server(capacity=4, chunk=4, fill_bytes=1.0).run(reqs, realtime=False)
+    assert [s.rid for s in served] == [0, 1, 2, 3, 4]
+    assert sum(1 for s in served if s.admitted < served[0].finished) >= 3     # held while the first ran
+
+
+def test_batch_hold_pauses_a_problem(rt):
+    """rt_batch_hold: a held problem does not advance; released, it finishes
+    with the same result as alone."""
+    pa, pb = si.lattice_problem(21, t_end=0.5), si.lattice_problem(28, t_end=0.5)
+    qa, qb = rt.rt_quad_product(2, 8), rt.rt_quad_product(2, 16)
+    b = rt.Batch([pa, pb], [qa, qb], order=2, integrator=rt.RT_HEUN, dts=[0.5 * pa.mesh.dx, 0.5 * pb.mesh.dx])
+    b.hold(1)
+    b.step(3)
+    assert b.progress(0)[0] == 3 and b.progress(1)[0] == 0
+    b.hold(1, False)
+    b.run()
+    s = rt.Solver(pb, qb, order=2, integrator=rt.RT_HEUN, dt=0.5 * pb.mesh.dx)
+    s.step()
+    assert np.array_equal(b.psi(1), s.psi())
+    s.close()
+    b.close()
