@@ -67,7 +67,8 @@ def bytes_per_update(order, integrator, storage, mesh="lattice"):
     return base
 
 
-KERNEL_SOURCES = {"cart": ["cart_kernel.cuh", "device_common.cuh"], "tri": ["tri_kernel.cu", "device_common.cuh"],
+KERNEL_SOURCES = {"cart": ["cart_kernel.cuh", "device_common.cuh"],
+                  "tri": ["tri_staged_kernel.cu", "tri_kernel.cu", "device_common.cuh"],
                   "tri2": ["tri2_kernel.cu", "device_common.cuh"]}
 
 
@@ -356,7 +357,8 @@ def run_ours(args, spec):
                      "frac": achieved_gbs / peak, "traffic": traffic,
                      "traffic_per": "step (all stage launches), DRAM read + write bytes",
                      "traffic_source": traffic_src,
-                     "kernel": {"cart": "cart_stage_kernel", "tri": "tri_stage_kernel",
+                     "kernel": {"cart": "cart_stage_kernel",
+                                "tri": "tri_staged_kernel" if info.variant == 3 else "tri_stage_kernel",
                                 "tri2": "tri_grad_kernel + tri_stage2_kernel"}[kind],
                      "bytes_per_update": bpu, "peak_source": f"{peak_src} hbm_gbs",
                      "achieved_basis": "algorithmic bytes per cell-ordinate x cell-ordinates x steps / event time of the steps"},
@@ -477,6 +479,25 @@ def run_sweep(args, w):
     rt.load_library()
     dp = w.get("dp", 1)
     jobs = sweep_jobs(rt, w["k"], w["grids"], dp=dp)
+    if args.profile_step:
+        # one batched step of the first --profile-step instances (for profilers): two untimed steps, then one
+        import torch
+        sub = jobs[:args.profile_step]
+        b = rt.Batch([j.problem for j in sub], [j.quad for j in sub], dts=[j.dt for j in sub],
+                     orders=[j.order for j in sub], integrators=[j.integrator for j in sub],
+                     tile_y=args.tile_y or 16)
+        b.step(1)
+        b.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.step(1)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": args.workload, "instances": len(sub), "tile_y": args.tile_y or 16,
+                          "ms_one_batched_step": e0.elapsed_time(e1)}))
+        b.close()
+        return
     # autotuned tiles: one rt_autotune per distinct shape for the one-at-a-time
     # path, and the batch-level segment length for the batched path
     shapes = {}
@@ -598,13 +619,24 @@ def serve_oracle_baseline(specs, budget_s, workers):
     import multiprocessing as mp
     order = sorted(range(len(specs)), key=lambda i: oracle_request_cost(specs[i]))
     chosen, tot = [], 0.0
+    seen = set()
     for i in order:
-        c = oracle_request_cost(specs[i])
+        sp = specs[i]
+        dup = sp.kind == "lattice" and (sp.n, sp.n_p, sp.n_phi, sp.t_end) in seen
+        c = 0.0 if dup else oracle_request_cost(sp)
         if tot + c > budget_s * workers:
             break
         chosen.append(i)
         tot += c
-    tasks = [(i, specs[i].kind, specs[i].n, specs[i].n_p, specs[i].n_phi, specs[i].t_end) for i in chosen]
+        if sp.kind == "lattice":
+            seen.add((sp.n, sp.n_p, sp.n_phi, sp.t_end))
+    # lattice requests with the same grid and ordinates are the same problem: solve each once
+    key = lambda i: (specs[i].kind, specs[i].n, specs[i].n_p, specs[i].n_phi, specs[i].t_end,
+                     i if specs[i].kind != "lattice" else -1)
+    first = {}
+    for i in chosen:
+        first.setdefault(key(i), i)
+    tasks = [(i, specs[i].kind, specs[i].n, specs[i].n_p, specs[i].n_phi, specs[i].t_end) for i in first.values()]
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in env_keys}
     for k in env_keys:
@@ -620,11 +652,13 @@ def serve_oracle_baseline(specs, budget_s, workers):
             else:
                 os.environ[k] = v
     wall = time.perf_counter() - t0
-    out = {rid: q for rid, q, _ in res}
+    by_key = {key(rid): q for rid, q, _ in res}
+    out = {i: by_key[key(i)] for i in chosen}
     kinds = collections.Counter(f"{specs[i].kind} {specs[i].n}^2 x {specs[i].n_p * specs[i].n_phi}" for i in chosen)
     desc = (f"FP64 numpy oracle, {workers} single-threaded processes, the {len(chosen)} cheapest of the "
-            f"{len(specs)} requests to their final times: " + ", ".join(f"{v} x {k}" for k, v in sorted(kinds.items())))
-    return out, len(chosen) / wall if wall > 0 else None, wall, desc
+            f"{len(specs)} requests to their final times ({len(tasks)} distinct problems): "
+            + ", ".join(f"{v} x {k}" for k, v in sorted(kinds.items())))
+    return out, len(tasks) / wall if wall > 0 else None, wall, desc
 
 
 def run_serve(args, w):
@@ -664,6 +698,15 @@ def run_serve(args, w):
     lat16 = [s.latency for s in res["bf16"]["served"]]
     latf = [s.latency for s in fifo]
     pf, p32 = SV.percentiles(latf), SV.percentiles(lat32)
+
+    def slowest(served, k=5):
+        out = []
+        for sv in sorted(served, key=lambda x: -x.latency)[:k]:
+            sp = specs[sv.rid]
+            out.append({"rid": sv.rid, "request": f"{sp.kind} {sp.n}^2 x {sp.n_p * sp.n_phi}",
+                        "arrival": round(sv.arrival, 3), "start": round(sv.admitted, 3),
+                        "finished": round(sv.finished, 3), "latency": round(sv.latency, 3)})
+        return out
     out = {
         "metric": "served solves/s", "value": count / res["fp32"]["span"], "unit": "solves/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": res["fp32"]["span"] * 1e3, "higher_is_better": True,
@@ -682,6 +725,7 @@ def run_serve(args, w):
         "latency_s": {"fp32": p32, "bf16": SV.percentiles(lat16), "plain_fifo_fp32": pf},
         "solves_per_s": {"fp32": count / res["fp32"]["span"], "bf16": count / res["bf16"]["span"],
                          "plain_fifo_fp32": count / span_fifo},
+        "slowest": {"fp32": slowest(res["fp32"]["served"]), "plain_fifo_fp32": slowest(fifo)},
         "p99_vs_plain": pf["p99"] / p32["p99"],
         "p50_vs_plain": pf["p50"] / p32["p50"],
         "qoi_rel_diff": {"bf16_vs_fp32_max": max(d_bf16), "bf16_vs_fp32_median": float(np.median(d_bf16)),
@@ -720,6 +764,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="Cartesian tiles from the library's model, not the autotuner")
+    ap.add_argument("--profile-step", type=int, default=0,
+                    help="sweeps: time one batched step of the first N instances and stop (for profilers)")
     ap.add_argument("--serve-policy", default="fcfs_fill", choices=["fcfs_fill", "all"])
     ap.add_argument("--serve-oracle-budget", type=float, default=150.0,
                     help="seconds of oracle work per host core for the serving stream's CPU baseline")

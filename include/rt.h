@@ -213,7 +213,9 @@ typedef struct {
   int32_t kind, order, integrator, storage;
   int32_t tile_x, tile_y, n_work_items, stages_per_step;
   int64_t device_bytes;
-  int32_t variant;   /* Cartesian kernel variant in use: 1 per-lane, 2 chunk-uniform (0: triangles) */
+  int32_t variant;   /* kernel variant in use: Cartesian 1 per-lane, 2 chunk-uniform directions;
+                        triangles 3 first order with each chunk's rows staged in shared memory,
+                        0 otherwise (rows gathered from global memory) */
   int32_t vec;       /* ordinates per lane */
   int32_t regrouped; /* Cartesian: 1 if the ordinates are stored regrouped by direction quadrant, each
                         quadrant padded with zero-weight ordinates to whole chunks (done when the
@@ -307,7 +309,11 @@ rt_status rt_set_state(rt_solver* s, const void* host, size_t bytes);
 /* Test hooks, not for production use: key "wait_limit_cycles" bounds every
  * device-side wait (default about two seconds of SM clock); key "drop_load"
  * (value q >= 0) makes the Cartesian kernel skip its q-th tile load, so that the
- * wait for it runs out and the launch reports RT_ETIMEOUT. value < 0 clears. */
+ * wait for it runs out and the launch reports RT_ETIMEOUT. value < 0 clears.
+ * Key "tri_staged" (first-order triangle solvers): 1 runs the stage with the
+ * kernel that stages each chunk's rows in shared memory (the default), 0 with
+ * the kernel that gathers neighbour rows from global memory; RT_EINVAL for
+ * other solvers. */
 rt_status rt_debug_set(rt_solver* s, const char* key, int64_t value);
 
 void rt_destroy(rt_solver* s);

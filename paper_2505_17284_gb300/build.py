@@ -24,7 +24,7 @@ LIB = os.path.join(LIBDIR, "librt_gb300.so")
 SOURCES = ["cart_f32_uni2v4.cu", "cart_bf16_uni2v4.cu", "cart_f32_uni2v2.cu", "cart_bf16_uni2v2.cu", "cart_f32_uni4.cu",
            "cart_bf16_uni4.cu", "cart_f32_lane.cu", "cart_bf16_lane.cu", "cart_dispatch.cu",
            "tri_kernel.cu", "host_common.cpp", "api.cpp", "batch.cpp", "quadrature.cpp", "noalloc.cu",
-           "autotune.cpp", "box_kernel.cu", "tri2_kernel.cu"]
+           "autotune.cpp", "box_kernel.cu", "tri2_kernel.cu", "tri_staged_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

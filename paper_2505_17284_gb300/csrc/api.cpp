@@ -202,7 +202,7 @@ rt_status rt_info(const rt_solver* s, rt_info_t* out) {
   out->n_work_items = (int32_t)I.stage_items.size();
   out->stages_per_step = I.integrator == RT_HEUN ? 2 : 1;
   out->device_bytes = s->arena.bytes;
-  out->variant = I.kind == RT_MESH_CARTESIAN ? (I.uni ? 2 : 1) : 0;
+  out->variant = I.kind == RT_MESH_CARTESIAN ? (I.uni ? 2 : 1) : (I.uni ? 3 : 0);
   out->vec = I.kind == RT_MESH_CARTESIAN ? I.cvec : I.vec;
   out->regrouped = I.regrouped;
   out->n_box_items = (int32_t)I.box_items.size();
@@ -394,6 +394,19 @@ rt_status rt_debug_set(rt_solver* s, const char* key, int64_t value) {
     if (v < 0) v = -1;
     D.drop_load = v;
     off = offsetof(InstDesc, drop_load);
+  } else if (std::strcmp(key, "tri_staged") == 0) {
+    // first-order triangles: 1 = the staged kernel, 0 = the gathering kernel (host-side choice)
+    if (s->I.kind != RT_MESH_TRIANGLES || s->I.order != 1 || !s->I.staged_ok) {
+      set_error("tri_staged applies to first-order triangle solvers with chunk halos");
+      return RT_EINVAL;
+    }
+    cudaStreamSynchronize(s->stream);
+    if (s->graph) {
+      cudaGraphExecDestroy(s->graph);
+      s->graph = nullptr;
+    }
+    s->I.uni = value != 0 ? 1 : 0;
+    return RT_OK;
   } else {
     set_error("unknown debug key '%s'", key);
     return RT_EINVAL;

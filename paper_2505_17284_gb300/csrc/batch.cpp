@@ -7,7 +7,13 @@
 // instead of one launch each. Problems can be added and removed between steps;
 // each slot owns its device memory (its own allocation list), freed on removal.
 // rt_batch_step enqueues up to n steps for the unfinished problems; while the
-// membership and n stay the same it replays one captured CUDA graph. Problems
+// membership and n stay the same it replays one captured CUDA graph (captured
+// at the second call with the same membership: a call right after a change
+// launches directly, since a serving loop may change the membership at every
+// call). Membership changes do not drain the stream: the new work list is
+// copied from pinned staging buffers behind the launches already queued, and a
+// replaced graph is destroyed at the next point where the stream is
+// synchronised anyway. Problems
 // past their own N_t are dropped from the work list at the next step and are
 // also masked on the device.
 #include <algorithm>
@@ -62,6 +68,14 @@ struct rt_batch {
   std::vector<int> members;           // slots in the current work list
   cudaGraphExec_t graph = nullptr;
   int64_t graph_n = 0;
+  bool fresh = false;                  // the work list was rebuilt at the last step call
+  std::vector<cudaGraphExec_t> old_graphs;   // replaced, destroyed once the stream is synchronised
+  // pinned staging of the work lists (a ring, so a copy still queued is not overwritten)
+  static constexpr int kStage = 4;
+  char* h_stage[kStage] = {};
+  size_t h_stage_cap[kStage] = {};
+  cudaEvent_t h_stage_ev[kStage] = {};
+  int h_next = 0;
   bool failed = false;
 };
 
@@ -72,13 +86,71 @@ rt_status batch_fail(rt_batch* b, rt_status st) {
   return st;
 }
 
+// Retire the current graph; launches of it may still be queued, so it is
+// destroyed by release_graphs once the stream has been synchronised.
+void release_graphs(rt_batch* b);
+
 void drop_graph(rt_batch* b) {
   if (b->graph) {
-    cudaStreamSynchronize(b->stream);
-    cudaGraphExecDestroy(b->graph);
+    b->old_graphs.push_back(b->graph);
     b->graph = nullptr;
   }
   b->graph_n = 0;
+  if (b->old_graphs.size() > 64) {   // bound the retired list
+    cudaStreamSynchronize(b->stream);
+    release_graphs(b);
+  }
+}
+
+// Destroy retired graphs. Call only after the stream has been synchronised.
+void release_graphs(rt_batch* b) {
+  for (cudaGraphExec_t g : b->old_graphs) cudaGraphExecDestroy(g);
+  b->old_graphs.clear();
+}
+
+// Copy `bytes` from host memory to `dst` on the batch's stream through the next
+// pinned staging buffer, without synchronising with the work already queued.
+rt_status stage_copy(rt_batch* b, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return RT_OK;
+  const int k = b->h_next;
+  b->h_next = (k + 1) % rt_batch::kStage;
+  if (!b->h_stage_ev[k] && cudaEventCreateWithFlags(&b->h_stage_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+    set_error("event creation failed");
+    return RT_ECUDA;
+  }
+  // the last copy out of this buffer must have been done (rarely still queued)
+  if (b->h_stage[k] && cudaEventSynchronize(b->h_stage_ev[k]) != cudaSuccess) {
+    set_error("waiting for a staging copy failed");
+    return RT_ECUDA;
+  }
+  if (b->h_stage_cap[k] < bytes) {
+    if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+    b->h_stage[k] = nullptr;
+    b->h_stage_cap[k] = 0;
+    const size_t cap = std::max<size_t>(bytes * 2, 64 << 10);
+    if (cudaHostAlloc((void**)&b->h_stage[k], cap, cudaHostAllocDefault) != cudaSuccess) {
+      b->h_stage[k] = nullptr;
+      set_error("pinned staging allocation of %zu bytes failed", cap);
+      return RT_ECUDA;
+    }
+    b->h_stage_cap[k] = cap;
+  }
+  std::memcpy(b->h_stage[k], src, bytes);
+  if (cudaMemcpyAsync(dst, b->h_stage[k], bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaEventRecord(b->h_stage_ev[k], b->stream) != cudaSuccess) {
+    set_error("copying a work list failed");
+    return RT_ECUDA;
+  }
+  return RT_OK;
+}
+
+void free_staging(rt_batch* b) {
+  for (int k = 0; k < rt_batch::kStage; ++k) {
+    if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+    if (b->h_stage_ev[k]) cudaEventDestroy(b->h_stage_ev[k]);
+    b->h_stage[k] = nullptr;
+    b->h_stage_ev[k] = nullptr;
+  }
 }
 
 // Build, validate and initialise a problem in slot `i`.
@@ -181,6 +253,7 @@ rt_status rebuild(rt_batch* b) {
   }
   if (items.size() > b->items_cap) {
     cudaStreamSynchronize(b->stream);
+    release_graphs(b);
     if (b->d_items) b->shared.release(b->d_items);
     b->d_items = nullptr;
     b->items_cap = 0;
@@ -193,6 +266,7 @@ rt_status rebuild(rt_batch* b) {
   }
   if (box_items.size() > b->box_cap) {
     cudaStreamSynchronize(b->stream);
+    release_graphs(b);
     if (b->d_box_list) b->shared.release(b->d_box_list);
     b->d_box_list = nullptr;
     b->box_cap = 0;
@@ -203,22 +277,12 @@ rt_status rebuild(rt_batch* b) {
     b->d_box_list = (WorkItem*)p;
     b->box_cap = cap;
   }
-  if (!box_items.empty() &&
-      cudaMemcpyAsync(b->d_box_list, box_items.data(), box_items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess) {
-    set_error("copying the box work list failed");
-    return RT_ECUDA;
-  }
-  if (!items.empty()) {
-    cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the host list goes out of scope
-    if (e != cudaSuccess) {
-      set_error("copying the work list failed: %s", cudaGetErrorString(e));
-      return RT_ECUDA;
-    }
-  }
+  // the launches already queued read the old lists before these copies (stream order)
+  rt_status cst = stage_copy(b, b->d_box_list, box_items.data(), box_items.size() * sizeof(WorkItem));
+  if (cst == RT_OK) cst = stage_copy(b, b->d_items, items.data(), items.size() * sizeof(WorkItem));
+  if (cst != RT_OK) return cst;
   b->dirty = false;
+  b->fresh = true;
   return RT_OK;
 }
 
@@ -242,7 +306,9 @@ rt_status step_members(rt_batch* b, int64_t n) {
     if (st != RT_OK) return st;
   }
   if (b->members.empty() || n <= 0) return RT_OK;
-  if (n >= kGraphMinSteps) {
+  const bool fresh = b->fresh;
+  b->fresh = false;
+  if (n >= kGraphMinSteps && !fresh) {
     if (!b->graph || b->graph_n != n) {
       drop_graph(b);
       cudaGraph_t g = nullptr;
@@ -319,6 +385,8 @@ rt_status rt_batch_create(int32_t k, const rt_problem* problems, int32_t capacit
     for (Slot& S : b->slots)
       if (S.arena) S.arena->free_all();
     b->shared.free_all();
+    release_graphs(b);
+    free_staging(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     return code;
@@ -366,6 +434,7 @@ rt_status rt_batch_remove(rt_batch* b, int32_t i) {
   if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
   drop_graph(b);
   cudaStreamSynchronize(b->stream);
+  release_graphs(b);
   Slot& S = b->slots[i];
   S.arena->free_all();
   S.arena.reset();
@@ -437,8 +506,9 @@ rt_status rt_batch_qoi(rt_batch* b, int32_t i, rt_qoi_t* out) {
   if (!slot_ok(b, i)) { set_error("slot %d is empty or out of range", i); return RT_EINVAL; }
   if (b->failed) { set_error("batch is in its error state"); return RT_ESTATE; }
   InstState h;
-  rt_status st = read_inst_state(b->slots[i].inst, b->stream, &h);
+  rt_status st = read_inst_state(b->slots[i].inst, b->stream, &h);   // synchronises the stream
   if (st != RT_OK) return batch_fail(b, st);
+  release_graphs(b);
   fill_qoi(b->slots[i].inst, h, out);
   return RT_OK;
 }
@@ -463,6 +533,8 @@ void rt_batch_destroy(rt_batch* b) {
   cudaStreamSynchronize(b->stream);
   (void)cudaGetLastError();
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  release_graphs(b);
+  free_staging(b);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (Slot& S : b->slots)
     if (S.arena) S.arena->free_all();

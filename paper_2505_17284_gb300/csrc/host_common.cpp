@@ -326,6 +326,64 @@ static void reorder_triangles(const rt_mesh* m, TriMeta& tm, std::vector<int32_t
   tm.geo2.swap(geo2);
 }
 
+// ---------------------------------------------------------------- chunk halos
+// Halo of each chunk of kTriStgChunk consecutive cells of the device order
+// (the staged first-order triangle kernel): the cells outside the chunk that
+// share an edge with one of its cells, sorted, padded per chunk to a multiple of
+// 4 ids (16-byte copies), and per cell the slots of its neighbours among the
+// chunk's staged rows. The staged kernel is used (I.uni = 1, I.ly = the largest
+// halo rounded up to 4) when every halo has at most kMaxChunkHalo cells.
+constexpr int kMaxChunkHalo = 128;
+
+static void build_chunk_halos(const TriMeta& tm, int64_t n_cells, Instance& I, std::vector<int2>& oc,
+                              std::vector<int32_t>& halo, std::vector<uint32_t>& lidx) {
+  constexpr int C = kTriStgChunk;
+  const int64_t n_chunks = (n_cells + C - 1) / C;
+  oc.assign(n_chunks, int2{0, 0});
+  halo.clear();
+  lidx.assign(n_chunks * C, 0xffffffffu);
+  int hmax = 0;
+  std::vector<int32_t> h;
+  for (int64_t k = 0; k < n_chunks; ++k) {
+    const int64_t c0 = k * C, c1 = std::min(n_cells, c0 + C);
+    h.clear();
+    for (int64_t c = c0; c < c1; ++c) {
+      const int nb[3] = {tm.nbr[c].x, tm.nbr[c].y, tm.nbr[c].z};
+      for (int e = 0; e < 3; ++e)
+        if (nb[e] >= 0 && (nb[e] < c0 || nb[e] >= c1)) h.push_back(nb[e]);
+    }
+    std::sort(h.begin(), h.end());
+    h.erase(std::unique(h.begin(), h.end()), h.end());
+    if ((int)h.size() > kMaxChunkHalo) {   // too wide for the staged kernel's buffers
+      oc.clear(); halo.clear(); lidx.clear();
+      I.uni = 0;
+      I.staged_ok = 0;
+      return;
+    }
+    hmax = std::max(hmax, (int)h.size());
+    oc[k] = int2{(int)halo.size(), (int)h.size()};
+    for (int64_t c = c0; c < c1; ++c) {
+      const int nb[3] = {tm.nbr[c].x, tm.nbr[c].y, tm.nbr[c].z};
+      uint32_t v = 0;
+      for (int e = 0; e < 3; ++e) {
+        uint32_t slot = 255;
+        if (nb[e] >= c0 && nb[e] < c1) {
+          slot = (uint32_t)(nb[e] - c0);
+        } else if (nb[e] >= 0) {
+          slot = (uint32_t)C + (uint32_t)(std::lower_bound(h.begin(), h.end(), nb[e]) - h.begin());
+        }
+        v |= slot << (8 * e);
+      }
+      lidx[c] = v;
+    }
+    halo.insert(halo.end(), h.begin(), h.end());
+    while (halo.size() % 4) halo.push_back(0);
+  }
+  I.uni = 1;
+  I.staged_ok = 1;
+  I.ly = (hmax + 3) & ~3;
+}
+
 // ---------------------------------------------------------------- tiles
 // Ordinates per lane: the largest V in {4, 2, 1} that divides M_pad/32 and for
 // which every group of V consecutive ordinates has one sign of xi (zero-weight
@@ -579,6 +637,9 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
 
   // --- triangles: mesh metadata
   TriMeta tm;
+  std::vector<int2> stg_halo_oc;
+  std::vector<int32_t> stg_halo;
+  std::vector<uint32_t> stg_lidx;
   if (I.kind == RT_MESH_TRIANGLES) {
     s = triangle_metadata(mesh, mat->cell_mat, mat->cell_region, tm);
     if (s != RT_OK) return s;
@@ -664,9 +725,20 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     I.cart_smem = cart_smem_bytes(order, storage, I.run, I.cvec, I.ly, stage_hi);
     if (I.cart_smem > 227 * 1024) { set_error("tile %dx%d needs %zu bytes of shared memory", I.tx, I.ly, I.cart_smem); return RT_EINVAL; }
   } else {
-    // persistent work items: item g processes 64-cell chunks g, g + G, ...
+    // persistent work items: item g processes 64-cell chunks g, g + G, ...; the
+    // staged first-order kernel runs two CTAs per SM, the others three
     const int64_t n_chunks = (n_cells + 63) / 64;
-    const int G = (int)std::min<int64_t>(n_chunks, 3LL * device_sm_count());
+    if (order == 1) {
+      build_chunk_halos(tm, n_cells, I, stg_halo_oc, stg_halo, stg_lidx);
+      // the staged kernel's two row buffers must fit the shared memory of a CTA
+      const int top = integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER;
+      if (I.staged_ok && tri_staged_smem_bytes(I.vec, storage, I.ly, top) > 108 * 1024) {
+        I.uni = 0;
+        I.staged_ok = 0;
+        stg_halo_oc.clear(); stg_halo.clear(); stg_lidx.clear();
+      }
+    }
+    const int G = (int)std::min<int64_t>(n_chunks, (I.uni ? 2LL : 3LL) * device_sm_count());
     I.stage_items.clear();
     for (int g = 0; g < G; ++g) {
       WorkItem w{};
@@ -764,6 +836,9 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   float4* d_geo = nullptr;
   float4* d_geo2 = nullptr;
   float* d_lg = nullptr;
+  int2* d_halo_oc = nullptr;
+  int32_t* d_halo = nullptr;
+  uint32_t* d_lidx = nullptr;
   if (I.kind == RT_MESH_CARTESIAN) {
     keep.emplace_back(2 * (size_t)n_cells);
     uint8_t* hm = reinterpret_cast<uint8_t*>(keep.back().data());
@@ -788,6 +863,25 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     d_geo = (float4*)p;
     RT_CUDA_TRY(cudaMemcpyAsync(d_nbr, hn, n_cells * sizeof(int4), cudaMemcpyHostToDevice, stream));
     RT_CUDA_TRY(cudaMemcpyAsync(d_geo, hg, 2 * n_cells * sizeof(float4), cudaMemcpyHostToDevice, stream));
+    if (I.staged_ok) {
+      // staged first-order kernel: chunk halos and neighbour slots
+      const size_t b_oc = stg_halo_oc.size() * sizeof(int2), b_h = stg_halo.size() * sizeof(int32_t),
+                   b_l = stg_lidx.size() * sizeof(uint32_t);
+      keep.emplace_back(b_oc + b_h + b_l);
+      char* hk = keep.back().data();
+      std::memcpy(hk, stg_halo_oc.data(), b_oc);
+      std::memcpy(hk + b_oc, stg_halo.data(), b_h);
+      std::memcpy(hk + b_oc + b_h, stg_lidx.data(), b_l);
+      if ((s = arena.get(b_oc, &p)) != RT_OK) return s;
+      d_halo_oc = (int2*)p;
+      if ((s = arena.get(std::max<size_t>(b_h, 16), &p)) != RT_OK) return s;
+      d_halo = (int32_t*)p;
+      if ((s = arena.get(b_l, &p)) != RT_OK) return s;
+      d_lidx = (uint32_t*)p;
+      RT_CUDA_TRY(cudaMemcpyAsync(d_halo_oc, hk, b_oc, cudaMemcpyHostToDevice, stream));
+      if (b_h) RT_CUDA_TRY(cudaMemcpyAsync(d_halo, hk + b_oc, b_h, cudaMemcpyHostToDevice, stream));
+      RT_CUDA_TRY(cudaMemcpyAsync(d_lidx, hk + b_oc + b_h, b_l, cudaMemcpyHostToDevice, stream));
+    }
     if (order == 2) {
       keep.emplace_back(3 * n_cells * sizeof(float4));
       std::memcpy(keep.back().data(), tm.geo2.data(), 3 * n_cells * sizeof(float4));
@@ -823,6 +917,8 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
   D.xi = d_quad; D.eta = d_quad + I.Mpad; D.w = d_quad + 2 * I.Mpad;
   D.tri_nbr = d_nbr; D.tri_geo = d_geo;
   D.tri_geo2 = d_geo2; D.tri_lg = d_lg;
+  D.tri_halo_oc = d_halo_oc; D.tri_halo = d_halo; D.tri_lidx = d_lidx;
+  D.tri_hmax = (I.kind == RT_MESH_TRIANGLES && I.staged_ok) ? I.ly : 0;
   D.st = I.st; D.partials = I.partials;
   D.kind = I.kind; D.order = order; D.integrator = integrator; D.storage = storage;
   D.nx = I.nx; D.ny = I.ny; D.M = I.M; D.Mpad = I.Mpad;
@@ -872,6 +968,8 @@ rt_status launch_step(const InstDesc* d_desc, const WorkItem* d_items, int n_ite
       e = launch_cart_stage(d_desc, d_items, n_items, stages[i], order, storage, run, cvec, ly_max, stream, uni);
     else if (order == 2)
       e = launch_tri2_stage(d_desc, d_items, n_items, stages[i], storage, std::min(vec, 2), vec, stream);
+    else if (uni)
+      e = launch_tri_staged(d_desc, d_items, n_items, stages[i], storage, vec, ly_max, stream);
     else
       e = launch_tri_stage(d_desc, d_items, n_items, stages[i], storage, vec, stream);
     if (e != cudaSuccess) {
@@ -903,8 +1001,18 @@ rt_status launch_init_all(const InstDesc* d_desc, const WorkItem* d_init_items, 
 }
 
 rt_status prepare_instance_kernels(const Instance& I, int ly_max) {
-  if (I.kind != RT_MESH_CARTESIAN) return RT_OK;
   const int stages[2] = {I.integrator == RT_HEUN ? STAGE_HEUN1 : STAGE_EULER, STAGE_HEUN2};
+  if (I.kind != RT_MESH_CARTESIAN) {
+    if (!I.staged_ok) return RT_OK;
+    for (int i = 0; i < (I.integrator == RT_HEUN ? 2 : 1); ++i) {
+      cudaError_t e = prepare_tri_staged(stages[i], I.storage, I.vec, ly_max);
+      if (e != cudaSuccess) {
+        set_error("kernel set-up failed: %s", cudaGetErrorString(e));
+        return RT_ECUDA;
+      }
+    }
+    return RT_OK;
+  }
   for (int i = 0; i < (I.integrator == RT_HEUN ? 2 : 1); ++i) {
     cudaError_t e = prepare_cart_stage(stages[i], I.order, I.storage, I.run, I.cvec, ly_max, I.uni);
     if (e != cudaSuccess) {

@@ -49,7 +49,9 @@ struct Instance {
   int64_t n_steps = 0;
   int32_t tx = 16, ly = 32, n_strips = 0, n_segs = 0;
   int32_t run = 2, cvec = 1;        // Cartesian kernel: cells per thread, ordinates per lane
-  int32_t uni = 0;                  // Cartesian kernel: chunk-uniform flow directions
+  int32_t uni = 0;                  // Cartesian kernel: chunk-uniform flow directions; triangles (first
+                                    // order): 1 = staged kernel (ly then holds the largest chunk halo)
+  int32_t staged_ok = 0;            // triangles: the staged kernel's metadata exists (test hook switches)
   // ordinate layout: 0 the caller's order; 1 regrouped by direction quadrant,
   // each quadrant padded to whole chunks (kmap: caller k -> slot; inv: slot ->
   // caller k or -1; device arrays, NULL for the caller's order)

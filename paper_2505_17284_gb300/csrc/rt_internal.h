@@ -27,6 +27,7 @@ constexpr int kQOut = kMaxReg + 1;     // index of the boundary outflow
 constexpr int NQ = kMaxReg + 2;        // QoI vector: abs[16], mass, outflow
 constexpr int kChunk = 32;             // ordinates per chunk (one per lane)
 constexpr int kMaxUniChunks = 64;      // chunk-uniform variant: at most this many ordinate chunks
+constexpr int kTriStgChunk = 32;       // cells per chunk of the staged first-order triangle kernel
 
 enum Stage : int32_t { STAGE_EULER = 0, STAGE_HEUN1 = 1, STAGE_HEUN2 = 2, STAGE_INIT = 3 };
 enum Kind : int32_t { KIND_CART = 0, KIND_TRI = 1 };
@@ -104,6 +105,17 @@ struct alignas(128) InstDesc {
   float* tri_lg;
   int32_t periodic_x;           // Cartesian: 1 if the x- and x+ sides are periodic (no boundary faces in x)
   int32_t periodic_y;           // Cartesian: 1 if the y- and y+ sides are periodic
+  // triangles, staged first-order kernel: per chunk of kTriStgChunk cells
+  // {offset, count} of its halo (the cells outside the chunk that share an edge
+  // with it; offsets are multiples of 4), the halo ids, and per cell the slots of
+  // its three neighbours among the chunk's staged rows (byte e: 0..31 the chunk's
+  // own cells, 32 + h halo cell h, 255 a boundary edge); tri_hmax = the largest
+  // halo (multiple of 4)
+  const int2* tri_halo_oc;
+  const int32_t* tri_halo;
+  const uint32_t* tri_lidx;
+  int32_t tri_hmax;
+  int32_t pad3;
 };
 
 struct WorkItem {
@@ -128,6 +140,12 @@ int cart_tile_width(int run);
 bool cart_variant_exists(int order, int run, int vec, int uni = 0);
 cudaError_t launch_tri_stage(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage,
                              int storage, int vec, cudaStream_t stream);
+// Staged first-order triangle stage (rows of a chunk's cells and halo in shared
+// memory, one 512-thread CTA per SM): hmax = the instances' largest halo.
+cudaError_t launch_tri_staged(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int stage, int storage,
+                              int vec, int hmax, cudaStream_t stream);
+cudaError_t prepare_tri_staged(int stage, int storage, int vec, int hmax);
+size_t tri_staged_smem_bytes(int vec, int storage, int hmax, int stage);
 cudaError_t launch_init(const InstDesc* d_desc, const WorkItem* d_items, int n_items, int vec,
                         int storage, cudaStream_t stream);
 // Second-order triangle stage: the limited-gradient kernel (grad_vec ordinates

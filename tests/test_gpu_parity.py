@@ -404,6 +404,55 @@ def test_enclosure_triangles(rt, integrator):
     check_qoi(q, acc, S, 4, scale=S["mass"] + sum(acc.abs_int))
 
 
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("integrator", ["euler", "heun"])
+@pytest.mark.parametrize("n_p,n_phi", [(2, 16), (4, 16), (8, 32), (6, 16)])
+def test_staged_triangle_kernel_matches_gathering_kernel(rt, n_p, n_phi, integrator, storage):
+    """First order on triangles: the kernel that stages each 32-cell chunk's
+    rows (own, halo, psi^n) in shared memory computes what the kernel that
+    gathers neighbour rows from global memory computes (the same operations
+    per element, some on FP32 pairs), and both match the oracle. 30^2 split
+    mesh (57 chunks, ragged last chunk), 32 to 256 ordinates (1, 2 and 4
+    ordinates per lane)."""
+    p = si.enclosure_problem(30, jitter=0.2, seed=5)
+    M = n_p * n_phi
+    psi0 = si.random_psi(p.mesh.n_cells, M, seed=31)
+    quad = rt.rt_quad_product(n_p, n_phi)
+    integ = rt.RT_HEUN if integrator == "heun" else rt.RT_EULER
+    out = {}
+    for staged in (1, 0):
+        s = rt.Solver(p, quad, order=1, integrator=integ, storage=storage)
+        rt.rt_debug_set(s.h, "tri_staged", staged)
+        assert rt.rt_info(s.h).variant == (3 if staged else 0)
+        s.set_psi(psi0)
+        s.step(5)
+        out[staged] = (s.psi(), s.qoi(), s.info.dt)
+        s.close()
+    a, b = out[1][0], out[0][0]
+    if storage == 0:
+        assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
+    else:
+        # the two kernels order some FP32 operations differently (ordinate pairs), so an
+        # element can round stochastically to the other neighbouring BF16 value: at most
+        # one BF16 unit apart (2^-7 relative at most), and rarely
+        assert np.all(np.abs(a - b) <= 2.0 ** -7 * np.maximum(np.abs(a), np.abs(b)))
+        assert rel_l2(a, b) <= 1e-3
+    if storage == 0:
+        op = oracle.TriangleOracle(p, oracle.product_quadrature(n_p, n_phi), order=1)
+        start = psi0.astype(np.float32).astype(np.float64)
+        ref, acc, S = oracle.run(op, start, out[1][2], 5, integrator)
+        assert rel_l2(a, ref) <= PSI_TOL
+        check_qoi(out[1][1], acc, S, len(S["abs"]), scale=S["mass"])
+
+
+def test_tri_staged_hook_rejects_other_solvers(rt):
+    s = rt.Solver(si.lattice_problem(14), rt.rt_quad_product(2, 8), dt=0.25)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_debug_set(s.h, "tri_staged", 0)
+    assert e.value.code == rt.RT_EINVAL
+    s.close()
+
+
 @pytest.mark.parametrize("n_p,n_phi", [(2, 16), (4, 16), (8, 32), (6, 16), (16, 32)])
 def test_triangle_random_state_vector_widths(rt, n_p, n_phi):
     """Random state, one Euler step, ordinate counts 32/64/256/96/512 (1, 2 and
