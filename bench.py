@@ -717,8 +717,9 @@ def run_serve(args, w):
                           "130, first order Euler), M in {64,128,256,512}",
                    "end_times": f"lattice {3.2 * horizon:g}, enclosure {2.6 * horizon:g}"
                                 + (" (the benchmarks' own)" if horizon == 1.0 else f" (x{horizon:g} of the benchmarks')"),
-                   "scheduler": policy + (" (oldest first, younger requests join while the advanced set moves at "
-                                          "most 2 GB of state per step; the rest held on the device)"
+                   "scheduler": policy + (" (oldest first; younger requests join while the advanced set moves at "
+                                          "most 2 GB of state per step and their remaining work is at most a quarter "
+                                          "of the oldest one's; the rest held on the device)"
                                           if policy == "fcfs_fill" else " (every admitted request advances)"),
                    "admission": "free slot (64), device memory within 85% of the free HBM at start and within the "
                                 "live free memory", "chunk_steps": 16, "step": "the whole stream"},

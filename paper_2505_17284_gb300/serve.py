@@ -11,12 +11,15 @@ from admission to retirement. Latency is retirement time minus arrival time.
 Which admitted problems the shared launches advance is the scheduler's
 choice (policy "fcfs_fill", the default): the oldest request always runs,
 and younger ones join it, oldest first, while the per-step state traffic of
-the chosen set stays within `fill_bytes` (the traffic that keeps the GPU
-busy); the others are held on the device (rt_batch_hold) until capacity frees
-up. Large requests thus run at nearly the speed they would have alone, in
-arrival order, while small requests fill the capacity that one large request
-leaves idle. Policy "all" advances every admitted problem together (processor
-sharing, which stretches large requests by the number sharing the GPU).
+the chosen set stays within `fill_bytes` and the remaining work of the joiners
+(state traffic of their remaining steps) adds up to at most `join_share` of
+the oldest one's; the others are held on the device (rt_batch_hold) until
+capacity frees up. Large requests thus run in arrival order at nearly the
+speed they would have alone (two large ones never share the GPU, which would
+delay the older one's finish and stretch the tail), while small requests ride
+along and finish early. Policy "all" advances every admitted problem together
+(processor sharing, which stretches large requests by the number sharing the
+GPU).
 
 The plain baseline is a first-in first-out server that solves one request
 at a time with the single-problem entry points, run against the same arrival
@@ -94,22 +97,29 @@ class Server:
     chunk: int = 16                # steps per enqueue
     policy: str = "fcfs_fill"      # or "all" (every admitted problem advances)
     fill_bytes: float = 2.0e9      # per-step state traffic of the advanced set (fcfs_fill)
+    join_share: float = 0.25       # joiners' remaining work, at most this share of the oldest's
     mem_fraction: float = 0.85     # of the device memory free at start: the server's budget
     reserve: int = 2 << 30         # bytes kept free for the allocator's own use
     max_ahead: int = 2             # chunks enqueued ahead of the device
     log: list = field(default_factory=list)
 
-    def select(self, active, weight):
-        """Slots to advance: all (policy "all"), or the oldest first while the
-        summed per-step traffic stays within fill_bytes (the oldest always)."""
+    def select(self, active, weight, remaining):
+        """Slots to advance: all (policy "all"), or the oldest, joined in
+        arrival order by requests that keep the per-step traffic within
+        fill_bytes and whose remaining work fits in join_share of the
+        oldest's remaining work."""
         order = sorted(active, key=lambda s: (active[s][0].arrival, active[s][0].rid))
         if self.policy == "all":
             return set(order)
-        chosen, acc = set(), 0.0
-        for s in order:
-            if not chosen or acc + weight[s] <= self.fill_bytes:
+        first = order[0]
+        chosen, acc = {first}, weight[first]
+        left = self.join_share * weight[first] * remaining[first]
+        for s in order[1:]:
+            work = weight[s] * remaining[s]
+            if acc + weight[s] <= self.fill_bytes and work <= left:
                 chosen.add(s)
                 acc += weight[s]
+                left -= work
         return chosen
 
     def run(self, requests, realtime=True):
@@ -150,7 +160,11 @@ class Server:
                     if pending:
                         time.sleep(max(0.0, pending[0].arrival - now()))
                     continue
-                run = self.select(active, weight)
+                remaining = {}
+                for slot in active:
+                    d, n = b.progress(slot)
+                    remaining[slot] = n - d
+                run = self.select(active, weight, remaining)
                 for slot in active:
                     h = slot not in run
                     if h != (slot in held):
