@@ -505,11 +505,11 @@ def run_sweep(args, w):
         shapes.setdefault((j.problem.mesh.nx, j.M), j)
     for j in shapes.values():
         autotune.tuned_config(j.problem, j.quad, j.order, j.integrator, rt.RT_FP32, j.dt, steps=3)
-    best_ty, ty_times = S.tune_batch(jobs, candidates=(0, 16, 24, 32, 48, 96), steps=3)
+    configs, group_table = S.tune_groups(jobs, tile_ys=(0, 16, 24, 32, 48), variants=(0, 1), steps=3)
     clocks = ClockSampler(0)
     clocks.start()
     phases = {}
-    qb, tb, steps_b = S.solve_batched(jobs, tile_y=best_ty, phases=phases)
+    qb, tb, steps_b = S.solve_batched(jobs, configs=configs, phases=phases)
     qp, tp, per, steps_p = S.solve_plain(jobs, tune=True)
     clk = clocks.stop()
     diff = max(S.qoi_rel_diff(a, b) for a, b in zip(qb, qp))
@@ -529,7 +529,9 @@ def run_sweep(args, w):
                        "sigma_s_ij": "blue blocks U[0,0.5], others U[0.5,1.5]", "materials": 49}),
                    "scheme": "MUSCL Heun", "psi_storage": "fp32",
                    "step": "one whole sweep (all instances to their N_t = 0.914 n)",
-                   "batch_tile_y": best_ty, "batch_tile_y_ms_per_step": ty_times,
+                   "batch_configs": group_table,
+                   "batch_configs_basis": "per group of one ordinate count: tile_y x variant (0 = library choice, "
+                                          "1 = per-lane directions), ms per step of that group alone",
                    "plain_tiles": "rt_autotune per shape", "l2": "working set of the large-grid instances > L2"},
         "plain": {"solves_per_s": k / tp, "seconds": tp, "path": "rt_create + rt_step(N_t) + rt_qoi + rt_destroy per instance"},
         "batched_seconds": tb,
@@ -544,11 +546,12 @@ def run_sweep(args, w):
                      "peak_source": peak_src},
         "e2e": {"value": k / tb, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": k * QOI_BYTES,
                 "includes": "batch creation from host arrays, all steps, QoI read-back, destroy"},
-        "gpu_launches": {"batched": (2 + box) * max(steps_b) * len({j.M for j in jobs}) + (1 + box) * k,
+        "gpu_launches": {"batched": (2 * len({j.M for j in jobs}) + box) * max(steps_b) + (1 + box) * k,
                          "plain": sum((2 + box) * n + 1 + box for n in steps_p),
-                         "basis": "batched: per step and kernel-variant group (one per ordinate count) 2 stage "
-                                  "launches and, with the QoI squares, 1 box launch; per instance 1 init (+1 initial "
-                                  "box launch); plain: the same per instance"},
+                         "basis": "batched, at most: per step 2 stage launches per kernel-variant group (at most one "
+                                  "per ordinate count) and, with the QoI squares, 1 box launch for all groups; per "
+                                  "instance 1 init (+1 initial box launch); plain: per step 2 stage launches (+1 box "
+                                  "launch), per instance 1 init (+1)"},
         "clocks": clk,
     }
     print(json.dumps(out))

@@ -287,12 +287,31 @@ rt_status rebuild(rt_batch* b) {
 }
 
 rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream) {
+  const size_t ng = b->groups.size();
+  auto last_stage = [&](size_t j) { return b->groups[j].integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER; };
   for (int64_t i = 0; i < n; ++i) {
     for (const Group& g : b->groups) {
       rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, g.integrator, b->storage, g.order,
-                                 g.run, g.cvec, g.ly_max, g.vec, stream, g.uni,
-                                 g.box_count ? b->d_box_list + g.box_offset : nullptr, g.box_count);
+                                 g.run, g.cvec, g.ly_max, g.vec, stream, g.uni, nullptr, 0);
       if (st != RT_OK) return st;
+    }
+    // QoI boxes once every group has stepped: one launch per run of consecutive
+    // groups that end the step with the same stage (their box items are
+    // contiguous in the list); each box reads only its own problem's state
+    for (size_t j = 0; j < ng;) {
+      const int stage = last_stage(j);
+      const int first = b->groups[j].box_offset;
+      int count = 0;
+      size_t k = j;
+      for (; k < ng && last_stage(k) == stage; ++k) count += b->groups[k].box_count;
+      if (count > 0) {
+        const cudaError_t e = launch_box_outflow(b->d_desc, b->d_box_list + first, count, stage, b->storage, stream);
+        if (e != cudaSuccess) {
+          set_error("box outflow launch failed: %s", cudaGetErrorString(e));
+          return RT_ECUDA;
+        }
+      }
+      j = k;
     }
   }
   return RT_OK;

@@ -475,7 +475,9 @@ class Batch:
 
     def __init__(self, problems=(), quads=(), order=2, integrator=RT_HEUN, storage=RT_FP32, dts=None,
                  tile_x=0, tile_y=0, use_torch_allocator=True, variant=0, vec=0, capacity=0, integrators=None,
-                 orders=None):
+                 orders=None, configs=None):
+        """configs: optional per-problem dicts of tile_y / variant / vec (rt_problem's
+        own kernel options; a missing or 0 value takes the batch option)."""
         keep = _Keep()
         k = len(problems)
         arr = (rt_problem * max(k, 1))()
@@ -483,7 +485,9 @@ class Batch:
         for i, (p, qd) in enumerate(zip(problems, quads)):
             o = order if orders is None else orders[i]
             ig = integrator if integrators is None else integrators[i]
-            arr[i], self.shapes[i] = make_problem(p, qd, keep, o, ig, 0.0 if dts is None else dts[i])
+            cf = {} if configs is None or configs[i] is None else configs[i]
+            arr[i], self.shapes[i] = make_problem(p, qd, keep, o, ig, 0.0 if dts is None else dts[i],
+                                                  cf.get("tile_y", 0), cf.get("variant", 0), cf.get("vec", 0))
         self.allocator = TorchAllocator() if use_torch_allocator else None
         opts = make_options(storage=storage, tile_x=tile_x, tile_y=tile_y, allocator=self.allocator, variant=variant,
                             vec=vec)

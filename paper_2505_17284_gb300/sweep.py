@@ -59,14 +59,14 @@ def solve_plain(jobs, storage=rt.RT_FP32, tune=True):
     return out, time.perf_counter() - t0, per, steps
 
 
-def solve_batched(jobs, storage=rt.RT_FP32, tile_y=0, phases=None):
+def solve_batched(jobs, storage=rt.RT_FP32, tile_y=0, phases=None, configs=None):
     """Solve the jobs together in one batch. Returns (QoI dicts, seconds from
     batch creation to the last QoI read, steps per job); `phases`, if a dict,
-    receives the seconds of creation, stepping and read-back."""
+    receives the seconds of creation, stepping and read-back. `configs`: per-job
+    kernel options (dicts of tile_y / variant / vec, as from tune_groups)."""
     _sync()
     t0 = time.perf_counter()
-    b = rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
-                 orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=tile_y)
+    b = _batch(jobs, storage, tile_y, configs)
     _sync()
     t1 = time.perf_counter()
     b.run()
@@ -81,29 +81,78 @@ def solve_batched(jobs, storage=rt.RT_FP32, tile_y=0, phases=None):
     return out, t3 - t0, [q["n_steps"] for q in out]
 
 
+def _batch(jobs, storage, tile_y=0, configs=None):
+    return rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
+                    orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=tile_y,
+                    configs=configs)
+
+
+def _ms_per_step(jobs, storage, steps, tile_y=0, configs=None):
+    """CUDA-event milliseconds per batch step after one warm-up step; None if
+    the options are invalid for some member (RT_EINVAL)."""
+    import torch
+    try:
+        b = _batch(jobs, storage, tile_y, configs)
+    except rt.RTError as e:
+        if e.code != rt.RT_EINVAL:
+            raise
+        return None
+    b.step(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    b.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    b.close()
+    return e0.elapsed_time(e1) / steps
+
+
+def group_key(j):
+    """Jobs that share a kernel-variant group of the batch under every option:
+    the same ordinate count, order and integrator."""
+    return (j.M, j.order, j.integrator)
+
+
+def tune_groups(jobs, storage=rt.RT_FP32, tile_ys=(0, 16, 24, 32, 48), variants=(0, 1), steps=3):
+    """Per-group tuner: for each group of jobs with one ordinate count, order
+    and integrator, the (tile_y, variant) pair with the shortest batch step,
+    timed on that group's jobs alone. Small grids with 4 quadrants of 64
+    ordinates, for example, run faster on the per-lane-direction kernel
+    (variant 1) than on the chunk-uniform one the library picks for large
+    grids. Returns (per-job config dicts, {group: {"tile_y/variant": ms}})."""
+    groups = {}
+    for i, j in enumerate(jobs):
+        groups.setdefault(group_key(j), []).append(i)
+    configs = [None] * len(jobs)
+    table = {}
+    for key, idx in groups.items():
+        sub = [jobs[i] for i in idx]
+        times = {}
+        for ty in tile_ys:
+            for var in variants:
+                cf = {"tile_y": ty, "variant": var}
+                ms = _ms_per_step(sub, storage, steps, configs=[cf] * len(sub))
+                if ms is not None:
+                    times[(ty, var)] = ms
+        best = min(times, key=times.get)
+        for i in idx:
+            configs[i] = {"tile_y": best[0], "variant": best[1]}
+        table["M%d_o%d_%s" % (key[0], key[1], "heun" if key[2] == rt.RT_HEUN else "euler")] = {
+            "best": {"tile_y": best[0], "variant": best[1]},
+            "ms_per_step": {"%d/%d" % tv: round(ms, 4) for tv, ms in times.items()}}
+    return configs, table
+
+
 def tune_batch(jobs, storage=rt.RT_FP32, candidates=(0, 16, 24, 32, 48, 64), steps=4):
     """Batch-level tuner: the segment length shared by the batch's Cartesian
     problems, timed with CUDA events over `steps` steps of the whole batch
     after one warm-up step. Returns (best tile_y, {tile_y: ms per step})."""
-    import torch
     times = {}
     for ty in candidates:
-        try:
-            b = rt.Batch([j.problem for j in jobs], [j.quad for j in jobs], storage=storage, dts=[j.dt for j in jobs],
-                         orders=[j.order for j in jobs], integrators=[j.integrator for j in jobs], tile_y=ty)
-        except rt.RTError as e:
-            if e.code != rt.RT_EINVAL:
-                raise
-            continue   # segment too long for the shared memory of some member
-        b.step(1)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        b.step(steps)
-        e1.record()
-        torch.cuda.synchronize()
-        times[ty] = e0.elapsed_time(e1) / steps
-        b.close()
+        ms = _ms_per_step(jobs, storage, steps, tile_y=ty)
+        if ms is not None:   # None: segment too long for the shared memory of some member
+            times[ty] = ms
     best = min(times, key=times.get)
     return best, times
 

@@ -263,18 +263,26 @@ def test_box_outflow_of_the_lattice_squares(rt, quad):
 
 
 @pytest.mark.parametrize("storage", [0, 1])
-def test_box_outflow_batched_equals_alone_bitwise(rt, storage):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_box_outflow_batched_equals_alone_bitwise(rt, storage, mixed):
     """Problems with and without boxes and with different N_t in one batch (so
     the box launches of finished problems are masked): every box value equals
-    the problem solved alone, bit for bit."""
+    the problem solved alone, bit for bit. The mixed case puts Euler and Heun
+    problems of both orders in one batch, so the box launch after a step covers
+    several kernel-variant groups, split where the last stage differs."""
     probs = [si.lattice_problem(28, t_end=0.6), si.lattice_problem(30, t_end=1.0), si.lattice_problem(35, t_end=1.4)]
     probs[1].extra = {}
     quads = [rt.rt_quad_product(2, 16), rt.rt_quad_product(4, 16), rt.rt_quad_product(2, 32)]
+    orders, integrators = [2, 2, 2], [rt.RT_HEUN] * 3
+    if mixed:
+        probs.append(si.lattice_problem(42, t_end=0.8))
+        quads.append(rt.rt_quad_product(4, 16))
+        orders, integrators = [1, 2, 2, 2], [rt.RT_EULER, rt.RT_HEUN, rt.RT_EULER, rt.RT_HEUN]
     dts = [0.5 * pr.mesh.dx for pr in probs]
-    b = rt.Batch(probs, quads, order=2, integrator=rt.RT_HEUN, dts=dts, storage=storage)
+    b = rt.Batch(probs, quads, dts=dts, storage=storage, orders=orders, integrators=integrators)
     b.run()
     for i, (pr, qd) in enumerate(zip(probs, quads)):
-        s = rt.Solver(pr, qd, order=2, integrator=rt.RT_HEUN, dt=dts[i], storage=storage)
+        s = rt.Solver(pr, qd, order=orders[i], integrator=integrators[i], dt=dts[i], storage=storage)
         s.step()
         a, c = b.qoi(i), s.qoi()
         s.close()

@@ -43,6 +43,33 @@ def test_sweep_batched_equals_one_at_a_time(rt):
     assert best in times and all(t > 0 for t in times.values())
 
 
+def test_group_tuner_configs_equal_alone_with_the_same_options(rt):
+    """The per-group tuner's options (tile_y and kernel variant per group of one
+    ordinate count) run in one batch, here with the variant alternated per
+    problem so that chunk-uniform and per-lane groups of one ordinate count
+    share the batch: each result equals the problem solved alone with the same
+    options, bit for bit."""
+    from paper_2505_17284_gb300 import sweep as S
+    from paper_2505_17284_gb300.sweep import Job
+    jobs = []
+    for inst in si.sweep_instances(6, seed=11, grids=(21, 28, 35), Ms=(128, 256)):
+        p = si.lattice_problem(inst.n, sigma_a_blue=inst.sigma_a, sigma_s_scatter=inst.sigma_s, t_end=0.6)
+        jobs.append(Job(p, rt.rt_quad_product(inst.n_p, inst.n_phi), 2, rt.RT_HEUN, 0.5 * p.mesh.dx))
+    configs, table = S.tune_groups(jobs, tile_ys=(0, 16), variants=(0, 1), steps=2)
+    assert len(table) == len({S.group_key(j) for j in jobs})
+    assert all(c is not None and c["variant"] in (0, 1) for c in configs)
+    configs = [dict(c, variant=i % 2) for i, c in enumerate(configs)]
+    qb, tb, nb = S.solve_batched(jobs, configs=configs)
+    for j, c, a in zip(jobs, configs, qb):
+        s = rt.Solver(j.problem, j.quad, order=j.order, integrator=j.integrator, dt=j.dt, tile_y=c["tile_y"],
+                      variant=c["variant"])
+        s.step()
+        b = s.qoi()
+        s.close()
+        for k in a:
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), (c, k)
+
+
 def test_dp2_sweep_batched_equals_one_at_a_time_and_the_oracle(rt):
     """A DP-2 sweep (49 block materials per instance) through the batched
     path: each result equals the instance solved alone, and a small one
