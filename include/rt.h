@@ -146,7 +146,10 @@ typedef void (*rt_free_fn)(void* ptr, void* ctx);
  *   variant: Cartesian kernel variant. 0 = chosen by the library; 1 = per-lane
  *     flow directions (any quadrature); 2 = chunk-uniform directions, usable when
  *     every chunk of ordinates has one sign of xi and one of eta (the product
- *     quadrature's quadrants are contiguous); RT_EINVAL if it is not.
+ *     quadrature's quadrants are contiguous); RT_EINVAL if it is not. The
+ *     library takes chunk-uniform directions where the chunks allow them, except
+ *     where only 32-cell strips would (2 ordinates per lane) on a grid of at most
+ *     1e5 cells: there the per-lane variant measured faster.
  *   vec: Cartesian ordinates per lane (1, 2 or 4; 0 = chosen by the library);
  *     RT_EINVAL if the quadrature does not allow it (see rt_info_t for the choice).
  *   alloc/free/alloc_ctx: device allocator (NULL = cudaMalloc/cudaFree).

@@ -685,11 +685,17 @@ rt_status build_instance(const rt_mesh* mesh, const rt_materials* mat, const rt_
     // 2 ordinates per lane: fewer face evaluations and shared-memory reads per
     // cell, but twice the chunks of 4 ordinates per lane. Chosen automatically
     // only when 4 ordinates per lane do not give uniform chunks (the 16-cell
-    // strips with 4 per lane measured faster where both apply).
+    // strips with 4 per lane measured faster where both apply), and only on
+    // grids of more than kWideMinCells cells: with 256 ordinates (quadrants of
+    // 64) the per-lane kernel measured faster on 70^2..280^2 grids (0.16 against
+    // 0.21 ms per step at 70^2, 0.31 against 0.34 at 280^2), the 32-cell strips
+    // on 560^2 (0.64 against 0.68) and 1400^2 (2.31 against 2.89).
+    constexpr int64_t kWideMinCells = 100000;
     bool wide = false;
     if (variant != 1 && (vec == 0 || vec == 2) && tile_x != 16) {
       const bool narrow4 = tile_x == 0 && vec == 0 && I.cvec >= 4 && chunks_uniform(quad, I.Mpad, 4, cdx, cdy);
-      wide = !narrow4 && chunks_uniform(quad, I.Mpad, 2, cdx, cdy);
+      const bool small = tile_x == 0 && variant == 0 && vec == 0 && n_cells <= kWideMinCells;
+      wide = !narrow4 && !small && chunks_uniform(quad, I.Mpad, 2, cdx, cdy);
     }
     if (wide) {
       I.uni = 1;

@@ -147,6 +147,22 @@ def test_kernel_variants(rt, n_p, n_phi, variant, tile_x, order):
     check_qoi(q, acc, S, 3, scale=S["mass"])
 
 
+@pytest.mark.parametrize("n,variant,tile_x", [(63, 1, 16), (320, 2, 32)])
+def test_library_kernel_choice_by_grid_size(rt, n, variant, tile_x):
+    """256 ordinates (quadrants of 64): the library runs small grids (at most
+    1e5 cells) on the per-lane kernel with 16-cell strips and larger ones on the
+    32-cell chunk-uniform kernel; an explicit tile_x 32 asks for the latter at
+    any size."""
+    p = si.lattice_problem(n)
+    quad = rt.rt_quad_product(8, 32)
+    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    assert (s.info.variant, s.info.tile_x) == (variant, tile_x)
+    s.close()
+    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, tile_x=32)
+    assert (s.info.variant, s.info.tile_x) == (2, 32)
+    s.close()
+
+
 def test_uniform_variant_rejected_for_mixed_chunks(rt):
     p = si.lattice_problem(14)
     xi = np.array([0.6, -0.6] * 32)
@@ -847,13 +863,15 @@ def test_autotune_rejects_triangles(rt):
 @pytest.mark.parametrize("N,n", [(4, 63), (8, 63), (22, 28)])
 def test_tessellation_quadrature_cartesian(rt, N, n):
     """The paper's tessellation rule (64, 256 and 1936 ordinates: per-lane,
-    32-cell chunk-uniform and 1-ordinate-per-lane kernels), MUSCL Heun from a
-    smooth state against the oracle."""
+    32-cell chunk-uniform (asked for with tile_x 32: on a grid this small the
+    library picks the per-lane kernel) and chunk-uniform kernels), MUSCL Heun
+    from a smooth state against the oracle."""
     p = si.lattice_problem(n)
     M = 4 * N * N
     psi0 = si.smooth_psi(p.mesh, M, seed=6)
     quad = rt.rt_quad_tessellation(N)
-    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx)
+    s = rt.Solver(p, quad, order=2, integrator=rt.RT_HEUN, dt=0.5 * p.mesh.dx, tile_x=32 if N == 8 else 0)
+    assert N != 8 or (s.info.variant == 2 and s.info.tile_x == 32)
     # 484 ordinates per quadrant: stored regrouped, each quadrant padded to 512
     assert s.info.regrouped == (N == 22) and (N != 22 or (s.info.M_pad == 2048 and s.info.variant == 2))
     s.set_psi(psi0)
