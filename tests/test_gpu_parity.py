@@ -456,17 +456,23 @@ def test_staged_triangle_kernel_matches_gathering_kernel(rt, n_p, n_phi, integra
     if storage == 0:
         assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
     else:
-        # the two kernels order some FP32 operations differently (ordinate pairs), so an
-        # element can round stochastically to the other neighbouring BF16 value: at most
-        # one BF16 unit apart (2^-7 relative at most), and rarely
-        assert np.all(np.abs(a - b) <= 2.0 ** -7 * np.maximum(np.abs(a), np.abs(b)))
+        # Both kernels take the same stochastic-rounding bits per (cell, ordinate, step,
+        # stage) but order some FP32 operations differently (scalar-flux sums, ordinate
+        # pairs): rarely an element rounds to the other neighbouring BF16 value, and the
+        # later steps carry that difference downstream. So the two agree nearly everywhere
+        # bit for bit and to the BF16 level in L2; each is checked against the oracle below.
+        assert np.mean(a != b) <= 1e-2
         assert rel_l2(a, b) <= 1e-3
+    op = oracle.TriangleOracle(p, oracle.product_quadrature(n_p, n_phi), order=1)
+    start = psi0.astype(np.float32).astype(np.float64)
+    ref, acc, S = oracle.run(op, start, out[1][2], 5, integrator)
     if storage == 0:
-        op = oracle.TriangleOracle(p, oracle.product_quadrature(n_p, n_phi), order=1)
-        start = psi0.astype(np.float32).astype(np.float64)
-        ref, acc, S = oracle.run(op, start, out[1][2], 5, integrator)
         assert rel_l2(a, ref) <= PSI_TOL
         check_qoi(out[1][1], acc, S, len(S["abs"]), scale=S["mass"])
+    else:
+        # BF16 level: each of the 5 stores (10 with Heun) rounds by at most one unit
+        # (2^-7 relative) with mean zero
+        assert rel_l2(a, ref) <= 2e-2 and rel_l2(b, ref) <= 2e-2
 
 
 def test_tri_staged_hook_rejects_other_solvers(rt):
