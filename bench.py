@@ -510,6 +510,7 @@ def run_sweep(args, w):
     clocks.start()
     phases = {}
     qb, tb, steps_b = S.solve_batched(jobs, configs=configs, phases=phases)
+    batched_launches = phases.pop("gpu_launches")
     qp, tp, per, steps_p = S.solve_plain(jobs, tune=True)
     clk = clocks.stop()
     diff = max(S.qoi_rel_diff(a, b) for a, b in zip(qb, qp))
@@ -546,12 +547,12 @@ def run_sweep(args, w):
                      "peak_source": peak_src},
         "e2e": {"value": k / tb, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": k * QOI_BYTES,
                 "includes": "batch creation from host arrays, all steps, QoI read-back, destroy"},
-        "gpu_launches": {"batched": (2 * len({j.M for j in jobs}) + box) * max(steps_b) + (1 + box) * k,
+        "gpu_launches": {"batched": batched_launches,
                          "plain": sum((2 + box) * n + 1 + box for n in steps_p),
-                         "basis": "batched, at most: per step 2 stage launches per kernel-variant group (at most one "
-                                  "per ordinate count) and, with the QoI squares, 1 box launch for all groups; per "
-                                  "instance 1 init (+1 initial box launch); plain: per step 2 stage launches (+1 box "
-                                  "launch), per instance 1 init (+1)"},
+                         "basis": "batched: rt_batch_launches (per step 2 stage launches per kernel-variant group and "
+                                  "1 QoI-box launch for all groups; per instance 1 initial-state launch and 1 initial "
+                                  "box launch); plain: per step 2 stage launches (+1 box launch), per instance 1 init "
+                                  "(+1)"},
         "clocks": clk,
     }
     print(json.dumps(out))
@@ -686,8 +687,9 @@ def run_serve(args, w):
     res = {}
     for name, stor in (("fp32", rt.RT_FP32), ("bf16", rt.RT_BF16)):
         reqs, _ = serve_requests(rt, count, horizon, stor, arrivals=arr)
-        served = SV.Server(storage=stor, policy=policy).run(reqs, realtime=True)
-        res[name] = {"served": served, "span": max(s.finished for s in served)}
+        srv = SV.Server(storage=stor, policy=policy)
+        served = srv.run(reqs, realtime=True)
+        res[name] = {"served": served, "span": max(s.finished for s in served), "launches": srv.launches}
     reqs, _ = serve_requests(rt, count, horizon, rt.RT_FP32, arrivals=arr)
     fifo = SV.serve_fifo(reqs, rt.RT_FP32, realtime=True)
     clk = clocks.stop()
@@ -737,7 +739,9 @@ def run_serve(args, w):
         "e2e": {"value": count / res["fp32"]["span"], "unit": "solves/s", "h2d_bytes_per_step": None,
                 "d2h_bytes_per_step": count * QOI_BYTES, "includes": "problem build on the host, admission, all steps, "
                                                                "QoI read-back, removal"},
-        "gpu_launches": None,
+        "gpu_launches": {"fp32": res["fp32"]["launches"], "bf16": res["bf16"]["launches"],
+                         "basis": "rt_batch_launches of the served batch: initial-state, stage and QoI-box launches "
+                                  "(the plain FIFO server's launches not included)"},
         "clocks": clk,
     }
     if not args.no_cpu_baseline:

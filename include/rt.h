@@ -410,6 +410,15 @@ rt_status rt_batch_hold(rt_batch* b, int32_t slot, int32_t hold);
  * synchronisation). RT_EINVAL for an empty slot. */
 rt_status rt_batch_progress(const rt_batch* b, int32_t slot, int64_t* steps_done, int64_t* n_steps);
 
+/* Kernel launches this batch has issued so far, counted as they are enqueued:
+ * one initial-state launch per added problem (plus one QoI-box launch if it
+ * has boxes), then per step the stage launches of every kernel-variant group
+ * (two with Heun, one with Euler) and one QoI-box launch per run of groups
+ * ending on the same stage; a graph replay counts every launch it holds. For
+ * reports of the work done on the device; no synchronisation. RT_EINVAL for
+ * NULL arguments. The paper has no counterpart. */
+rt_status rt_batch_launches(const rt_batch* b, int64_t* n);
+
 /* Synchronise and copy the QoIs of the problem in `slot`. */
 rt_status rt_batch_qoi(rt_batch* b, int32_t slot, rt_qoi_t* out);
 

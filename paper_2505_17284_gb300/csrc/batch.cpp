@@ -68,6 +68,8 @@ struct rt_batch {
   std::vector<int> members;           // slots in the current work list
   cudaGraphExec_t graph = nullptr;
   int64_t graph_n = 0;
+  int64_t graph_launches = 0;          // kernel launches in one replay of the graph
+  int64_t launches = 0;                // kernel launches issued or replayed so far (rt_batch_launches)
   bool fresh = false;                  // the work list was rebuilt at the last step call
   std::vector<cudaGraphExec_t> old_graphs;   // replaced, destroyed once the stream is synchronised
   // pinned staging of the work lists (a ring, so a copy still queued is not overwritten)
@@ -205,6 +207,7 @@ rt_status add_in_slot(rt_batch* b, const rt_problem& P, int i) {
   if ((st = launch_init_all(b->d_desc + i, S.d_init_items, (int)I.init_items.size(), S.d_box_items, (int)hb.size(),
                             I.vec, I.storage, b->stream)) != RT_OK)
     return undo(st);
+  b->launches += hb.empty() ? 1 : 2;
   InstState h;
   if ((st = read_inst_state(I, b->stream, &h)) != RT_OK) return undo(st);
   S.used = true;
@@ -286,14 +289,16 @@ rt_status rebuild(rt_batch* b) {
   return RT_OK;
 }
 
-rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream) {
+rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream, int64_t* count) {
   const size_t ng = b->groups.size();
+  int64_t cnt = 0;
   auto last_stage = [&](size_t j) { return b->groups[j].integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER; };
   for (int64_t i = 0; i < n; ++i) {
     for (const Group& g : b->groups) {
       rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, g.integrator, b->storage, g.order,
                                  g.run, g.cvec, g.ly_max, g.vec, stream, g.uni, nullptr, 0);
       if (st != RT_OK) return st;
+      cnt += g.integrator == RT_HEUN ? 2 : 1;
     }
     // QoI boxes once every group has stepped: one launch per run of consecutive
     // groups that end the step with the same stage (their box items are
@@ -310,10 +315,12 @@ rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream) {
           set_error("box outflow launch failed: %s", cudaGetErrorString(e));
           return RT_ECUDA;
         }
+        ++cnt;
       }
       j = k;
     }
   }
+  *count = cnt;
   return RT_OK;
 }
 
@@ -335,7 +342,8 @@ rt_status step_members(rt_batch* b, int64_t n) {
         set_error("graph capture could not start");
         return RT_ECUDA;
       }
-      rt_status st = enqueue_steps(b, n, b->cap_stream);
+      int64_t cnt = 0;
+      rt_status st = enqueue_steps(b, n, b->cap_stream, &cnt);
       cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
       if (st != RT_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -350,14 +358,18 @@ rt_status step_members(rt_batch* b, int64_t n) {
         return RT_ECUDA;
       }
       b->graph_n = n;
+      b->graph_launches = cnt;
     }
     cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
     if (e != cudaSuccess) {
       set_error("graph launch failed: %s", cudaGetErrorString(e));
       return RT_ECUDA;
     }
+    b->launches += b->graph_launches;
   } else {
-    rt_status st = enqueue_steps(b, n, b->stream);
+    int64_t cnt = 0;
+    rt_status st = enqueue_steps(b, n, b->stream, &cnt);
+    b->launches += cnt;
     if (st != RT_OK) return st;
   }
   for (int i : b->members) {
@@ -507,6 +519,13 @@ rt_status rt_batch_run(rt_batch* b, int64_t max_steps) {
     }
     budget -= phase;
   }
+  return RT_OK;
+}
+
+rt_status rt_batch_launches(const rt_batch* b, int64_t* n) {
+  clear_error();
+  if (!b || !n) { set_error("batch or output is NULL"); return RT_EINVAL; }
+  *n = b->launches;
   return RT_OK;
 }
 

@@ -135,6 +135,7 @@ SIGNATURES = {
     "rt_batch_hold": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "rt_batch_step": (C.c_int, [C.c_void_p, C.c_int64]),
     "rt_batch_progress": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "rt_batch_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "rt_batch_run": (C.c_int, [C.c_void_p, C.c_int64]),
     "rt_batch_qoi": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(rt_qoi_t)]),
     "rt_batch_get_psi": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64]),
@@ -518,6 +519,11 @@ class Batch:
         done, total = C.c_int64(), C.c_int64()
         check(_fns().rt_batch_progress(self.h, slot, C.byref(done), C.byref(total)))
         return done.value, total.value
+
+    def launches(self) -> int:
+        n = C.c_int64()
+        check(_fns().rt_batch_launches(self.h, C.byref(n)))
+        return n.value
 
     def run(self, max_steps=0):
         check(_fns().rt_batch_run(self.h, int(max_steps)))

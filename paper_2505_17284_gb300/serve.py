@@ -102,6 +102,7 @@ class Server:
     reserve: int = 2 << 30         # bytes kept free for the allocator's own use
     max_ahead: int = 2             # chunks enqueued ahead of the device
     log: list = field(default_factory=list)
+    launches: int = 0              # kernel launches of the last run (rt_batch_launches)
 
     def select(self, active, weight, remaining):
         """Slots to advance: all (policy "all"), or the oldest, joined in
@@ -192,7 +193,10 @@ class Server:
                 elif len(events) > self.max_ahead:
                     events.popleft().synchronize()
         finally:
-            b.close()
+            try:
+                self.launches = b.launches()
+            finally:
+                b.close()
         return done
 
 

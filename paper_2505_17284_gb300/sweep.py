@@ -62,7 +62,8 @@ def solve_plain(jobs, storage=rt.RT_FP32, tune=True):
 def solve_batched(jobs, storage=rt.RT_FP32, tile_y=0, phases=None, configs=None):
     """Solve the jobs together in one batch. Returns (QoI dicts, seconds from
     batch creation to the last QoI read, steps per job); `phases`, if a dict,
-    receives the seconds of creation, stepping and read-back. `configs`: per-job
+    receives the seconds of creation, stepping and read-back and the kernel
+    launches of the batch (rt_batch_launches). `configs`: per-job
     kernel options (dicts of tile_y / variant / vec, as from tune_groups)."""
     _sync()
     t0 = time.perf_counter()
@@ -73,11 +74,12 @@ def solve_batched(jobs, storage=rt.RT_FP32, tile_y=0, phases=None, configs=None)
     _sync()
     t2 = time.perf_counter()
     out = [b.qoi(i) for i in range(len(jobs))]
+    launches = b.launches()
     b.close()
     _sync()
     t3 = time.perf_counter()
     if phases is not None:
-        phases.update(create=t1 - t0, run=t2 - t1, read_and_destroy=t3 - t2)
+        phases.update(create=t1 - t0, run=t2 - t1, read_and_destroy=t3 - t2, gpu_launches=launches)
     return out, t3 - t0, [q["n_steps"] for q in out]
 
 

@@ -802,6 +802,24 @@ def test_batch_add_remove_between_steps(rt):
     b.close()
 
 
+def test_batch_launch_count(rt):
+    """rt_batch_launches counts what the batch enqueues: two Heun problems of one
+    kernel variant, one with the QoI squares (2 + 1 initial launches), then per
+    step 2 stage launches and 1 box launch, the same whether a call launches
+    directly (the first after a membership change) or replays a graph."""
+    probs = [si.lattice_problem(28, t_end=3.2), si.lattice_problem(30, t_end=3.2)]
+    probs[1].extra = {}
+    quads = [rt.rt_quad_product(4, 16), rt.rt_quad_product(4, 16)]
+    b = rt.Batch(probs, quads, order=2, integrator=rt.RT_HEUN, dts=[0.5 * pr.mesh.dx for pr in probs])
+    assert b.launches() == 3
+    b.step(1)             # rebuilt work list: direct launches
+    assert b.launches() == 3 + 3
+    b.step(4)             # captured graph
+    b.step(4)             # replayed graph
+    assert b.launches() == 3 + 3 + 2 * 4 * 3
+    b.close()
+
+
 def test_batch_capacity_and_empty_slots(rt):
     p = si.lattice_problem(14)
     p.t_end = 0.3
