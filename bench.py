@@ -481,21 +481,28 @@ def run_sweep(args, w):
     jobs = sweep_jobs(rt, w["k"], w["grids"], dp=dp)
     if args.profile_step:
         # one batched step of the first --profile-step instances (for profilers): two untimed steps, then one
+        # inside cudaProfilerStart/Stop (for ncu --profile-from-start off); --profile-tuned takes the per-group
+        # options of tune_groups (timed before the profiled region) instead of one tile_y for the batch
         import torch
         sub = jobs[:args.profile_step]
+        configs, table = (S.tune_groups(sub, steps=2) if args.profile_tuned else (None, None))
         b = rt.Batch([j.problem for j in sub], [j.quad for j in sub], dts=[j.dt for j in sub],
                      orders=[j.order for j in sub], integrators=[j.integrator for j in sub],
-                     tile_y=args.tile_y or 16)
+                     tile_y=0 if args.profile_tuned else (args.tile_y or 16), configs=configs)
         b.step(1)
         b.step(1)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = b.launches()
+        torch.cuda.profiler.start()
         e0.record()
         b.step(1)
         e1.record()
         torch.cuda.synchronize()
-        print(json.dumps({"workload": args.workload, "instances": len(sub), "tile_y": args.tile_y or 16,
-                          "ms_one_batched_step": e0.elapsed_time(e1)}))
+        torch.cuda.profiler.stop()
+        print(json.dumps({"workload": args.workload, "instances": len(sub),
+                          "options": table if args.profile_tuned else {"tile_y": args.tile_y or 16},
+                          "launches": b.launches() - n0, "ms_one_batched_step": e0.elapsed_time(e1)}))
         b.close()
         return
     # autotuned tiles: one rt_autotune per distinct shape for the one-at-a-time
@@ -774,6 +781,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="Cartesian tiles from the library's model, not the autotuner")
     ap.add_argument("--profile-step", type=int, default=0,
                     help="sweeps: time one batched step of the first N instances and stop (for profilers)")
+    ap.add_argument("--profile-tuned", action="store_true",
+                    help="with --profile-step: the per-group options of the sweep's tuner")
     ap.add_argument("--serve-policy", default="fcfs_fill", choices=["fcfs_fill", "all"])
     ap.add_argument("--serve-oracle-budget", type=float, default=150.0,
                     help="seconds of oracle work per host core for the serving stream's CPU baseline")
