@@ -137,6 +137,8 @@ def tune_groups(jobs, storage=rt.RT_FP32, tile_ys=(0, 16, 24, 32, 48), variants=
                 ms = _ms_per_step(sub, storage, steps, configs=[cf] * len(sub))
                 if ms is not None:
                     times[(ty, var)] = ms
+        if not times:
+            raise ValueError(f"no (tile_y, variant) pair is valid for the jobs with M, order, integrator = {key}")
         best = min(times, key=times.get)
         for i in idx:
             configs[i] = {"tile_y": best[0], "variant": best[1]}
