@@ -512,7 +512,9 @@ def run_sweep(args, w):
         shapes.setdefault((j.problem.mesh.nx, j.M), j)
     for j in shapes.values():
         autotune.tuned_config(j.problem, j.quad, j.order, j.integrator, rt.RT_FP32, j.dt, steps=3)
-    configs, group_table = S.tune_groups(jobs, tile_ys=(0, 16, 24, 32, 48), variants=(0, 1), steps=3)
+    by_shape = args.batch_tune == "shape"
+    configs, group_table = S.tune_groups(jobs, tile_ys=(0, 16, 24, 32, 48), variants=(0, 1), steps=3,
+                                         by_shape=by_shape)
     clocks = ClockSampler(0)
     clocks.start()
     phases = {}
@@ -538,8 +540,9 @@ def run_sweep(args, w):
                    "scheme": "MUSCL Heun", "psi_storage": "fp32",
                    "step": "one whole sweep (all instances to their N_t = 0.914 n)",
                    "batch_configs": group_table,
-                   "batch_configs_basis": "per group of one ordinate count: tile_y x variant (0 = library choice, "
-                                          "1 = per-lane directions), ms per step of that group alone",
+                   "batch_configs_basis": "per group of one ordinate count" + (" and grid" if by_shape else "")
+                                          + ": tile_y x variant (0 = library choice, 1 = per-lane directions), ms "
+                                          "per step of that group alone",
                    "plain_tiles": "rt_autotune per shape", "l2": "working set of the large-grid instances > L2"},
         "plain": {"solves_per_s": k / tp, "seconds": tp, "path": "rt_create + rt_step(N_t) + rt_qoi + rt_destroy per instance"},
         "batched_seconds": tb,
@@ -781,6 +784,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="Cartesian tiles from the library's model, not the autotuner")
     ap.add_argument("--profile-step", type=int, default=0,
                     help="sweeps: time one batched step of the first N instances and stop (for profilers)")
+    ap.add_argument("--batch-tune", default="group", choices=["group", "shape"],
+                    help="sweeps: tune kernel options per group of one ordinate count, or per ordinate count and grid")
     ap.add_argument("--profile-tuned", action="store_true",
                     help="with --profile-step: the per-group options of the sweep's tuner")
     ap.add_argument("--serve-policy", default="fcfs_fill", choices=["fcfs_fill", "all"])

@@ -116,16 +116,17 @@ def group_key(j):
     return (j.M, j.order, j.integrator)
 
 
-def tune_groups(jobs, storage=rt.RT_FP32, tile_ys=(0, 16, 24, 32, 48), variants=(0, 1), steps=3):
+def tune_groups(jobs, storage=rt.RT_FP32, tile_ys=(0, 16, 24, 32, 48), variants=(0, 1), steps=3, by_shape=False):
     """Per-group tuner: for each group of jobs with one ordinate count, order
-    and integrator, the (tile_y, variant) pair with the shortest batch step,
-    timed on that group's jobs alone. Small grids with 4 quadrants of 64
-    ordinates, for example, run faster on the per-lane-direction kernel
-    (variant 1) than on the chunk-uniform one the library picks for large
-    grids. Returns (per-job config dicts, {group: {"tile_y/variant": ms}})."""
+    and integrator (and, with by_shape, one cell count), the (tile_y, variant)
+    pair with the shortest batch step, timed on that group's jobs alone. Small
+    grids with 4 quadrants of 64 ordinates, for example, run faster on the
+    per-lane-direction kernel (variant 1) than on the chunk-uniform one the
+    library picks for large grids. Returns (per-job config dicts, {group:
+    {"tile_y/variant": ms}})."""
     groups = {}
     for i, j in enumerate(jobs):
-        groups.setdefault(group_key(j), []).append(i)
+        groups.setdefault(group_key(j) + ((j.n_cells,) if by_shape else ()), []).append(i)
     configs = [None] * len(jobs)
     table = {}
     for key, idx in groups.items():
@@ -142,7 +143,8 @@ def tune_groups(jobs, storage=rt.RT_FP32, tile_ys=(0, 16, 24, 32, 48), variants=
         best = min(times, key=times.get)
         for i in idx:
             configs[i] = {"tile_y": best[0], "variant": best[1]}
-        table["M%d_o%d_%s" % (key[0], key[1], "heun" if key[2] == rt.RT_HEUN else "euler")] = {
+        name = "M%d_o%d_%s" % (key[0], key[1], "heun" if key[2] == rt.RT_HEUN else "euler")
+        table[name + ("_cells%d" % key[3] if by_shape else "")] = {
             "best": {"tile_y": best[0], "variant": best[1]},
             "ms_per_step": {"%d/%d" % tv: round(ms, 4) for tv, ms in times.items()}}
     return configs, table

@@ -15,6 +15,7 @@ class FakeJob:
     M: int
     order: int = 2
     integrator: int = rt.RT_HEUN
+    n_cells: int = 4900
 
 
 def _fake_timer(table, calls):
@@ -65,3 +66,17 @@ def test_a_group_with_no_valid_pair_is_an_error(monkeypatch):
     monkeypatch.setattr(S, "_ms_per_step", lambda *a, **k: None)
     with pytest.raises(ValueError):
         S.tune_groups([FakeJob(64)], tile_ys=(16,), variants=(0,), steps=1)
+
+
+def test_by_shape_splits_groups_by_cell_count(monkeypatch):
+    jobs = [FakeJob(256, n_cells=4900), FakeJob(256, n_cells=313600), FakeJob(256, n_cells=4900)]
+    best = {4900: (16, 1), 313600: (48, 0)}
+
+    def timer(sub, storage, steps, tile_y=0, configs=None):
+        cells = {j.n_cells for j in sub}
+        assert len(cells) == 1
+        return 1.0 if (configs[0]["tile_y"], configs[0]["variant"]) == best[cells.pop()] else 2.0
+    monkeypatch.setattr(S, "_ms_per_step", timer)
+    configs, out = S.tune_groups(jobs, tile_ys=(16, 48), variants=(0, 1), steps=1, by_shape=True)
+    assert [(c["tile_y"], c["variant"]) for c in configs] == [(16, 1), (48, 0), (16, 1)]
+    assert set(out) == {"M256_o2_heun_cells4900", "M256_o2_heun_cells313600"}
