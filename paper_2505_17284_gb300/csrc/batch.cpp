@@ -289,16 +289,18 @@ rt_status rebuild(rt_batch* b) {
   return RT_OK;
 }
 
-rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream, int64_t* count) {
+// Enqueue n steps of the current work list on `stream`; *launched counts the
+// kernel launches enqueued (also when a launch fails part way).
+rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream, int64_t* launched) {
   const size_t ng = b->groups.size();
-  int64_t cnt = 0;
+  *launched = 0;
   auto last_stage = [&](size_t j) { return b->groups[j].integrator == RT_HEUN ? STAGE_HEUN2 : STAGE_EULER; };
   for (int64_t i = 0; i < n; ++i) {
     for (const Group& g : b->groups) {
       rt_status st = launch_step(b->d_desc, b->d_items + g.offset, g.count, g.kind, g.integrator, b->storage, g.order,
                                  g.run, g.cvec, g.ly_max, g.vec, stream, g.uni, nullptr, 0);
       if (st != RT_OK) return st;
-      cnt += g.integrator == RT_HEUN ? 2 : 1;
+      *launched += g.integrator == RT_HEUN ? 2 : 1;
     }
     // QoI boxes once every group has stepped: one launch per run of consecutive
     // groups that end the step with the same stage (their box items are
@@ -306,21 +308,20 @@ rt_status enqueue_steps(rt_batch* b, int64_t n, cudaStream_t stream, int64_t* co
     for (size_t j = 0; j < ng;) {
       const int stage = last_stage(j);
       const int first = b->groups[j].box_offset;
-      int count = 0;
+      int n_box = 0;
       size_t k = j;
-      for (; k < ng && last_stage(k) == stage; ++k) count += b->groups[k].box_count;
-      if (count > 0) {
-        const cudaError_t e = launch_box_outflow(b->d_desc, b->d_box_list + first, count, stage, b->storage, stream);
+      for (; k < ng && last_stage(k) == stage; ++k) n_box += b->groups[k].box_count;
+      if (n_box > 0) {
+        const cudaError_t e = launch_box_outflow(b->d_desc, b->d_box_list + first, n_box, stage, b->storage, stream);
         if (e != cudaSuccess) {
           set_error("box outflow launch failed: %s", cudaGetErrorString(e));
           return RT_ECUDA;
         }
-        ++cnt;
+        ++*launched;
       }
       j = k;
     }
   }
-  *count = cnt;
   return RT_OK;
 }
 
